@@ -1,0 +1,137 @@
+"""CPU oracle for the Guidefill shell fill — TEST INFRASTRUCTURE ONLY.
+
+Only ``tests/``, ``__graft_entry__.smoke()`` and ``bench.py``'s CPU-baseline leg
+may import this package.  The product library never calls it.  The C source
+``guidefill_oracle.c`` is compiled with gcc (no fast-math, no FP contraction)
+into ``liboracle.so`` beside it on first use, or by ``build()``.
+
+Functions follow the paper (arxiv 1611.05319):
+  fill       Algorithm 1 with the rotated ghost-pixel ball, eq. weight,
+             eq. bilinearDef, eqs. confidence / ready (smart order)
+  guidance   guide field from splines, Section 3.3
+  alg_bytes  algorithmic bytes of a fill under Algorithm 1's per-step semantics
+  frozen_fill / fill_backward   (see the adjoint section below)
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "guidefill_oracle.c")
+_SRC_ADJ = os.path.join(_HERE, "guidefill_oracle_adjoint.c")
+_LIB = os.path.join(_HERE, "liboracle.so")
+
+GHOST = 1
+SMART = 2
+
+KNOWN, UNFILLED, BYSTANDER = -1, -2, -3
+
+
+class Stats(C.Structure):
+    _fields_ = [("shells", C.c_int32), ("stalls", C.c_int32), ("evaluations", C.c_int64),
+                ("filled", C.c_int64), ("unreachable", C.c_int64), ("max_front", C.c_int64),
+                ("min_margin", C.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+def build(force: bool = False) -> str:
+    srcs = [s for s in (_SRC, _SRC_ADJ) if os.path.exists(s)]
+    newest = max(os.path.getmtime(s) for s in srcs)
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < newest:
+        tmp = _LIB + f".tmp{os.getpid()}"
+        cmd = ["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared",
+               "-o", tmp] + srcs + ["-lm"]
+        subprocess.run(cmd, check=True)
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+_lib = None
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        _lib = C.CDLL(build())
+        P = C.c_void_p
+        _lib.oracle_fill.restype = C.c_int
+        _lib.oracle_fill.argtypes = [C.c_int, C.c_int, C.c_int, P, P, P, C.c_double, C.c_double,
+                                     C.c_double, C.c_uint, C.c_float, C.c_int, P, P, P, P]
+        _lib.oracle_guidance.restype = C.c_int
+        _lib.oracle_guidance.argtypes = [C.c_int, C.c_int, P, C.c_int, P, P, C.c_float, P]
+        _lib.oracle_alg_bytes.restype = C.c_int64
+        _lib.oracle_alg_bytes.argtypes = [C.c_int, C.c_int, P, P, C.c_double, C.c_uint, C.c_float,
+                                          P, P]
+        if hasattr(_lib, "oracle_frozen_fill"):
+            _lib.oracle_frozen_fill.restype = C.c_int
+            _lib.oracle_frozen_fill.argtypes = [C.c_int, C.c_int, C.c_int, P, P, P, P, C.c_double,
+                                                C.c_double, C.c_float, P, P, P, C.c_int, P]
+            _lib.oracle_fill_backward.restype = C.c_int
+            _lib.oracle_fill_backward.argtypes = [C.c_int, C.c_int, C.c_int, P, P, P, P, C.c_double,
+                                                  C.c_double, C.c_float, P, P, C.c_int, P, P, P, P]
+    return _lib
+
+
+def _p(a):
+    return a.ctypes.data_as(C.c_void_p) if a is not None else None
+
+
+def _f32(x):
+    return float(np.float32(x))
+
+
+def fill(rgb, labels, guide, eps=3.0, mu=50.0, c=0.05, ghost=True, smart=True, tau=1e-5,
+         max_shells=0):
+    """Runs Algorithm 1 on a copy of ``rgb`` (float32/64 [H, W, C]) in FP64.
+    Parameters are rounded to FP32 first (the library takes FP32 parameters).
+    Returns dict(u=float64 [H, W, C], shell, enter, stall_steps, stats, status)."""
+    lab = np.ascontiguousarray(labels, np.uint8)
+    H, W = lab.shape
+    u = np.ascontiguousarray(rgb, np.float64).copy()
+    Cn = u.shape[2]
+    g = np.ascontiguousarray(guide, np.float32)
+    assert g.shape == (H, W, 2)
+    shell = np.empty((H, W), np.int32)
+    enter = np.empty((H, W), np.int32)
+    n_hole = int((lab == 1).sum())
+    cap = max_shells if max_shells > 0 else n_hole + 1
+    stall = np.zeros(cap + 1, np.uint8)
+    st = Stats()
+    flags = (GHOST if ghost else 0) | (SMART if smart else 0)
+    rc = lib().oracle_fill(H, W, Cn, _p(u), _p(lab), _p(g), _f32(eps), _f32(mu), _f32(c), flags,
+                           _f32(tau), int(max_shells), _p(shell), _p(enter), _p(stall),
+                           C.byref(st))
+    if rc < 0:
+        raise ValueError("oracle_fill: bad arguments")
+    s = st.as_dict()
+    return dict(u=u, shell=shell, enter=enter, stall_steps=stall[:s["shells"]].copy(), stats=s,
+                status=rc)
+
+
+def guidance(labels, offsets, pts, eta=3.0, H=None, W=None):
+    """Guide field from polylines (Section 3.3), float32 [H, W, 2]; zero outside
+    the hole."""
+    lab = np.ascontiguousarray(labels, np.uint8)
+    H, W = lab.shape
+    off = np.ascontiguousarray(offsets, np.int32)
+    P = np.ascontiguousarray(pts, np.float32)
+    g = np.zeros((H, W, 2), np.float32)
+    rc = lib().oracle_guidance(H, W, _p(lab), len(off) - 1, _p(off), _p(P), _f32(eta), _p(g))
+    if rc != 0:
+        raise ValueError("oracle_guidance: bad arguments")
+    return g
+
+
+def alg_bytes(labels, guide, eps, shell, enter, ghost=True, tau=1e-5):
+    lab = np.ascontiguousarray(labels, np.uint8)
+    H, W = lab.shape
+    g = np.ascontiguousarray(guide, np.float32)
+    return int(lib().oracle_alg_bytes(H, W, _p(lab), _p(g), _f32(eps), GHOST if ghost else 0,
+                                      _f32(tau), _p(np.ascontiguousarray(shell, np.int32)),
+                                      _p(np.ascontiguousarray(enter, np.int32))))

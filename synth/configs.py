@@ -1,0 +1,88 @@
+"""The five synthetic workloads (seeded), built only from ``synth`` primitives.
+
+Each builder returns a dict with
+  rgb     float32 [H, W, 3]  input image; hole and bystander pixels are set to
+                             NaN when ``poison`` is true (they must never be read)
+  gt      float32 [H, W, 3]  the image before the hole was cut (ground truth)
+  labels  uint8   [H, W]     0 known, 1 hole, 2 bystander
+  guide   float32 [H, W, 2]  only for constant-guidance workloads, else None
+  splines (offsets, pts)     polylines for the guidance-field sampler, else None
+  eps, mu, c, eta            parameters
+Guidance fields from splines are *not* built here: they are the sampler's job.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+from . import (annulus_mask, bands_with_fraction, const_guide, flatten_beziers, labels_from,
+               polygon_image, rect_mask, _rng)
+
+
+def _finish(img, hole, bystander=None, poison=False, **kw):
+    labels = labels_from(hole, bystander)
+    rgb = img.copy()
+    if poison:
+        rgb[labels != 0] = np.nan
+    d = dict(rgb=rgb, gt=img, labels=labels, guide=None, splines=None,
+             eps=3.0, mu=50.0, c=0.05, eta=3.0)
+    d.update(kw)
+    return d
+
+
+def plain_128(seed: int = 1, poison: bool = False):
+    """128x128 polygons + N(0, 0.01) noise; annulus hole of width 8 px centred
+    (radii 24..32); constant guidance at 30 degrees; eps=3, mu=50."""
+    H = W = 128
+    img = polygon_image(H, W, 8, seed)
+    hole = annulus_mask(H, W, 24.0, 32.0)
+    return _finish(img, hole, poison=poison, guide=const_guide(H, W, 30.0))
+
+
+def frame_1080(seed: int = 2, poison: bool = False, H: int = 1080, W: int = 1920,
+               fraction: float = 0.03):
+    """1920x1080 piecewise-smooth frame; hole = union of bands of width U[3, 15] px
+    along 20 cubic Beziers, about 3% of the pixels; eps=3, mu=50."""
+    img = polygon_image(H, W, 40, seed)
+    ctrl, hws, hole = bands_with_fraction(H, W, 20, seed, (1.5, 7.5), fraction)
+    return _finish(img, hole, poison=poison, splines=flatten_beziers(ctrl), half_widths=hws)
+
+
+def frame_4k_blob(seed: int = 3, poison: bool = False, H: int = 2160, W: int = 3840,
+                  blob: int = 400, fraction: float = 0.02):
+    """3840x2160 frame with one blob x blob square hole at a random position
+    plus thin bands along 20 Beziers; eps=4, mu=50."""
+    img = polygon_image(H, W, 40, seed)
+    ctrl, hws, hole = bands_with_fraction(H, W, 20, seed, (1.5, 7.5), fraction)
+    rng = _rng(seed + 31337)
+    bx = int(rng.integers(64, W - blob - 64))
+    by = int(rng.integers(64, H - blob - 64))
+    hole = hole | rect_mask(H, W, bx, by, blob, blob)
+    return _finish(img, hole, poison=poison, splines=flatten_beziers(ctrl), half_widths=hws,
+                   eps=4.0, blob_xy=(bx, by))
+
+
+def batch_frame(seed: int, poison: bool = False, H: int = 1080, W: int = 1920):
+    """One frame of the uneven batch: hole fraction U[0.5%, 8%], band widths
+    U[2, 40] px (half-widths U[1, 20])."""
+    rng = _rng(seed + 4242)
+    frac = float(rng.uniform(0.005, 0.08))
+    img = polygon_image(H, W, 40, seed)
+    ctrl, hws, hole = bands_with_fraction(H, W, 20, seed, (1.0, 20.0), frac)
+    return _finish(img, hole, poison=poison, splines=flatten_beziers(ctrl), half_widths=hws,
+                   target_fraction=frac)
+
+
+def batch_1080(n: int = 64, seed0: int = 100, poison: bool = False, H: int = 1080, W: int = 1920):
+    """The batched workload: n frames, seeds seed0 .. seed0+n-1."""
+    return [batch_frame(seed0 + i, poison=poison, H=H, W=W) for i in range(n)]
+
+
+def diff_frame(seed: int, poison: bool = False, H: int = 512, W: int = 512):
+    """One 512x512 frame of the differentiable workload: thin bands, ~5% of pixels."""
+    img = polygon_image(H, W, 12, seed)
+    ctrl, hws, hole = bands_with_fraction(H, W, 12, seed, (1.5, 4.5), 0.05, margin=24.0)
+    return _finish(img, hole, poison=poison, splines=flatten_beziers(ctrl), half_widths=hws)
+
+
+def diff_batch(n: int = 16, seed0: int = 200, poison: bool = False):
+    return [diff_frame(seed0 + i, poison=poison) for i in range(n)]
