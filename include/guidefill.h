@@ -1,0 +1,221 @@
+/*
+ * guidefill.h -- C ABI of the GB300 Guidefill shell-fill library (libguidefill.so).
+ *
+ * Guidefill (Hocking, MacKenzie, Schoenlieb, arxiv 1611.05319) fills an
+ * inpainting domain D_h shell by shell (Algorithm 1): at step k every pixel of
+ * the active boundary whose smart-order confidence exceeds c (eqs. confidence,
+ * ready) gets the normalised weighted average (eq. weight) of bilinearly
+ * interpolated "ghost pixels" (eq. bilinearDef) on a ball of radius eps rotated
+ * to the guide direction g(x) (Notation: B~ = R(B)).  This library runs that
+ * fill, the Section 3.3 guide-field construction from splines, and the adjoint
+ * of the fill, as hand-written CUDA kernels for sm_103a.
+ *
+ * Conventions for every entry point:
+ *  - All array pointers are DEVICE pointers owned by the caller, unless the
+ *    name says "host".  Images are row-major [H][W] with no padding; pixel
+ *    (x, y) is column x, row y, centre at integer coordinates.
+ *  - Colours are float RGBA, 16-byte aligned ([H][W][4]); all four channels
+ *    are filled alike.  Labels are uint8: 0 known, 1 hole (D_h),
+ *    2 bystander (B_h, Section 2.1; never read, never written).
+ *  - Guide fields are float [H][W][2] vectors g = (gx, gy) in pixel units
+ *    along x (columns) and y (rows); only hole pixels are read.
+ *  - `stream` is a cudaStream_t passed as void*; NULL is the legacy default
+ *    stream.  Every call is asynchronous on that stream and never synchronises
+ *    the host.  Device-side outcomes (status, shell counts) are written to a
+ *    caller-owned device gf_stats array.
+ *  - A call that returns GF_ERR_ARG detected the problem on the host and
+ *    launched nothing.  GF_ERR_CUDA means a CUDA API call failed (the CUDA
+ *    error is retrievable with gf_last_cuda_error()).
+ *  - A gf_ctx owns the library's scratch memory (it grows on demand with
+ *    cudaMalloc) and cached CUDA graphs; it is not thread safe: use one
+ *    context per host thread / concurrent stream.
+ */
+#ifndef GUIDEFILL_H
+#define GUIDEFILL_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    GF_OK = 0,
+    GF_INCOMPLETE = 1,       /* some hole pixels could never be filled (walled off) */
+    GF_ERR_ARG = -1,         /* invalid argument, detected on the host, nothing launched */
+    GF_ERR_CUDA = -2,        /* a CUDA runtime call failed */
+    GF_ERR_TIMEOUT = -3,     /* reserved: a bounded device wait gave up */
+    GF_ERR_NO_PROGRESS = -4, /* the shell loop hit max_shells before finishing */
+    GF_ERR_OOM = -5,         /* scratch allocation failed */
+    GF_ERR_UNSUPPORTED = -6, /* device is not sm_103 / feature unavailable */
+    GF_ERR_INTERNAL = -7     /* a device-side consistency check failed */
+} gf_status;
+
+/* gf_params.flags */
+#define GF_FLAG_GHOST 1u  /* rotated ghost-pixel ball (Guidefill); off = lattice ball (coherence transport) */
+#define GF_FLAG_SMART 2u  /* smart order, ready = C(x) > c (eq. ready); off = onion order */
+#define GF_FLAG_RESCAN 4u /* recompute the whole active boundary every step ("without tracking", Section 3.6) */
+
+/* Opaque library context. */
+typedef struct gf_ctx gf_ctx;
+
+/*
+ * One frame.  out_rgba may equal rgba (in-place fill; the fill never reads a
+ * hole pixel's input colour).  out_shell receives, per pixel: -1 known,
+ * -3 bystander, -2 hole pixel never filled, k >= 0 the step at which it was
+ * filled.  Optional outputs (NULL to skip):
+ *   out_enter [H][W] int32: step at which a hole pixel joined the active
+ *             boundary (Notation, d_active D^(k)_h), -1 never / not a hole;
+ *   out_stall uint32 bitmap of ceil((H*W+1)/32) words: bit k set when step k
+ *             was filled by the stall rule (no front pixel was ready).
+ */
+typedef struct {
+    int32_t H, W;
+    const float *rgba;      /* [H][W][4] input colours */
+    const uint8_t *labels;  /* [H][W] */
+    const float *guide;     /* [H][W][2] */
+    float *out_rgba;        /* [H][W][4] */
+    int32_t *out_shell;     /* [H][W] */
+    int32_t *out_enter;     /* [H][W] or NULL */
+    uint32_t *out_stall;    /* bitmap or NULL */
+} gf_frame;
+
+/*
+ * Method parameters (Section 3.2 defaults: eps = 3 px, mu = 50; Section 3.5:
+ * c = 0.05).  eps in [1, 7] px (ball radius in pixels, real valued: the ball
+ * is {(n,m) != 0 : n^2 + m^2 <= eps^2}); mu >= 0; c in (0, 1) for smart order;
+ * snap_tau: ghost-sample offsets within snap_tau of an integer are snapped to
+ * it (0 <= snap_tau < 0.01; default 1e-5); max_shells: safety cap on the
+ * number of steps (0 = number of hole pixels + 1).
+ */
+typedef struct {
+    float eps, mu, c;
+    uint32_t flags;
+    float snap_tau;
+    int32_t max_shells;
+} gf_params;
+
+/* Per-frame device-side results. */
+typedef struct {
+    int32_t shells;      /* K: steps that filled at least one pixel */
+    int32_t stalls;      /* steps filled by the stall rule */
+    int32_t status;      /* gf_status of this frame */
+    int32_t reserved;
+    int64_t filled;      /* hole pixels filled */
+    int64_t evaluations; /* ready tests executed (implementation count) */
+    int64_t max_front;   /* max over k of |d_active D^(k)_h| */
+    int64_t holes;       /* |D_h| */
+} gf_stats;
+
+/* Creates a context bound to CUDA device `device` (must be compute capability
+ * 10.3).  Returns GF_ERR_UNSUPPORTED on another device, GF_ERR_CUDA if the
+ * device cannot be used. */
+gf_status gf_create(gf_ctx **ctx, int device);
+
+/* Frees the context, its scratch memory and cached graphs.  Waits for work the
+ * context launched to finish.  NULL is ignored. */
+void gf_destroy(gf_ctx *ctx);
+
+/* Static string for a gf_status value. */
+const char *gf_status_string(int status);
+
+/* Last CUDA error code seen by the context (0 if none). */
+int gf_last_cuda_error(const gf_ctx *ctx);
+
+/*
+ * Fills one frame (Algorithm 1 with Guidefill's ball and weights).
+ * dev_stats: device pointer to one gf_stats, written when the fill ends.
+ */
+gf_status gf_fill(gf_ctx *ctx, const gf_frame *frame, const gf_params *params, gf_stats *dev_stats,
+                  void *stream);
+
+/*
+ * Fills n independent frames in one persistent launch: each thread-block
+ * cluster takes frames from a device work queue (largest hole first) and runs
+ * that frame's shell loop, so frames of very different hole sizes and shell
+ * counts overlap.  frames: HOST array of n descriptors; dev_stats: device
+ * array of n gf_stats.  The launch sequence is captured once into a CUDA graph
+ * and replayed while the descriptors and parameters stay the same.
+ */
+gf_status gf_fill_batched(gf_ctx *ctx, int n, const gf_frame *frames, const gf_params *params,
+                          gf_stats *dev_stats, void *stream);
+
+/*
+ * gf_fill_batched that also records two caller-owned CUDA events
+ * (cudaEvent_t passed as void*, NULL to skip) on `stream` immediately before
+ * and after the persistent fill kernel, outside the cached graphs, so that
+ * the kernel's own duration can be timed per call.  A measurement hook of
+ * this implementation (no counterpart in the paper).
+ */
+gf_status gf_fill_batched_ex(gf_ctx *ctx, int n, const gf_frame *frames, const gf_params *params,
+                             gf_stats *dev_stats, void *stream, void *event_fill_start,
+                             void *event_fill_end);
+
+/*
+ * gf_fill_batched with HOST buffers (pageable or pinned): the whole step a
+ * caller with frames in host memory makes.  Per frame i it copies rgba[i]
+ * ([H][W][4] float), labels[i] and either guide[i] ([H][W][2] float) or, when
+ * host_guide is NULL or host_guide[i] is NULL, the polylines (n_splines[i],
+ * host_offsets[i], n_points[i], host_pts[i]) to device scratch owned by the
+ * context; builds the guide field from the polylines if needed
+ * (gf_guidance_from_splines with `eta`); fills; and copies the filled image
+ * and shell map back into host_out_rgba[i] / host_out_shell[i].  host_stats:
+ * n gf_stats written on the host.  Synchronises `stream` before returning.
+ */
+gf_status gf_fill_batched_host(gf_ctx *ctx, int n, const int32_t *H, const int32_t *W,
+                               const float *const *host_rgba, const uint8_t *const *host_labels,
+                               const float *const *host_guide, const int32_t *n_splines,
+                               const int32_t *const *host_offsets, const int32_t *n_points,
+                               const float *const *host_pts, float eta, float *const *host_out_rgba,
+                               int32_t *const *host_out_shell, const gf_params *params,
+                               gf_stats *host_stats, void *stream);
+
+/*
+ * Guide field from splines (Section 3.3): for each hole pixel, the nearest
+ * segment of the polylines (offsets[n_splines+1] into pts[n_points][2], (x,y)
+ * pairs); if its distance d <= 3 eta, g = unit tangent * exp(-d^2/(2 eta^2)),
+ * else g = 0.  The nearest segment and the 3-eta cut are decided in FP32
+ * (ties: lowest segment index); the value is evaluated in FP64 and rounded once.
+ * Writes guide [H][W][2] at hole pixels only.
+ */
+gf_status gf_guidance_from_splines(gf_ctx *ctx, int H, int W, const uint8_t *labels, int n_splines,
+                                   const int32_t *offsets, int n_points, const float *pts, float eta,
+                                   float *guide, void *stream);
+
+/* One frame of a batched guide-field request. */
+typedef struct {
+    int32_t H, W;
+    const uint8_t *labels;
+    int32_t n_splines, n_points;
+    const int32_t *offsets; /* device [n_splines+1] */
+    const float *pts;       /* device [n_points][2] */
+    float *guide;           /* device [H][W][2] */
+} gf_spline_frame;
+
+/* gf_guidance_from_splines for n frames in one launch sequence; frames is a
+ * HOST array. */
+gf_status gf_guidance_batched(gf_ctx *ctx, int n, const gf_spline_frame *frames, float eta,
+                              void *stream);
+
+/*
+ * Launch shape of the persistent fill (no counterpart in the paper; a tuning
+ * knob of this implementation).  cluster_size in {0 (automatic), 1, 2, 4, 8,
+ * 16} CTAs per frame; n_clusters = number of persistent clusters (0 = as many
+ * as fit, capped at the number of frames); use_graph = capture the batched
+ * launch sequence into a CUDA graph and replay it (streams other than the
+ * legacy default stream only).  Results do not depend on the launch shape.
+ */
+gf_status gf_set_launch_config(gf_ctx *ctx, int cluster_size, int n_clusters, int use_graph);
+
+/* Launch shape chosen by the last fill call on this context. */
+gf_status gf_get_last_launch(const gf_ctx *ctx, int *cluster_size, int *n_clusters);
+
+/* Number of clusters of `cluster_size` CTAs that can be resident at once for
+ * a fill with this eps (0 if the size cannot be launched; -1 on bad ctx). */
+int gf_max_active_clusters(gf_ctx *ctx, float eps, int cluster_size);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GUIDEFILL_H */

@@ -1,0 +1,252 @@
+"""GB300-native Guidefill shell fill (arxiv 1611.05319): PyTorch-facing binding.
+
+PyTorch provides device memory and streams only; every step of the fill runs in
+the CUDA kernels of ``libguidefill.so`` behind the C ABI in
+``include/guidefill.h``.  This module marshals tensors into that ABI.
+
+    ctx = Context(0)
+    out = ctx.fill(rgba, labels, guide, eps=3.0, mu=50.0, c=0.05)
+    out.rgba, out.shell, out.stats()
+"""
+from __future__ import annotations
+
+import ctypes as C
+from dataclasses import dataclass, field
+from typing import List, Optional, Sequence
+
+import numpy as np
+import torch
+
+from . import _lib
+from ._lib import STATS_BYTES, STATS_DTYPE, GuidefillError, check, lib, make_params
+
+__all__ = ["Context", "context", "fill", "fill_batched", "guidance", "FillResult", "GuidefillError",
+           "to_rgba", "STATS_DTYPE"]
+
+
+def _ptr(t: Optional[torch.Tensor]):
+    return None if t is None else C.c_void_p(t.data_ptr())
+
+
+def _stream(stream) -> C.c_void_p:
+    s = torch.cuda.current_stream() if stream is None else stream
+    return C.c_void_p(s.cuda_stream)
+
+
+def to_rgba(img: torch.Tensor) -> torch.Tensor:
+    """[H, W, 3|4] float32 -> contiguous [H, W, 4] float32 (alpha = 1 when padded)."""
+    if img.dim() != 3 or img.shape[2] not in (3, 4):
+        raise ValueError("image must be [H, W, 3] or [H, W, 4]")
+    img = img.to(torch.float32)
+    if img.shape[2] == 3:
+        img = torch.cat([img, torch.ones_like(img[..., :1])], dim=2)
+    return img.contiguous()
+
+
+@dataclass
+class FillResult:
+    rgba: torch.Tensor
+    shell: torch.Tensor
+    enter: Optional[torch.Tensor]
+    stall: Optional[torch.Tensor]
+    _stats_dev: torch.Tensor = field(repr=False)
+
+    def stats(self) -> dict:
+        """Synchronises with the device and returns the frame's gf_stats."""
+        rec = np.frombuffer(self._stats_dev.cpu().numpy().tobytes(), dtype=STATS_DTYPE)[0]
+        d = {k: int(rec[k]) for k in STATS_DTYPE.names if k != "reserved"}
+        return d
+
+    def stall_steps(self) -> np.ndarray:
+        """Boolean array over steps 0..K-1: step filled by the stall rule."""
+        K = self.stats()["shells"]
+        bits = self.stall.cpu().numpy().view(np.uint32)
+        idx = np.arange(K)
+        return ((bits[idx >> 5] >> (idx & 31)) & 1).astype(bool)
+
+
+class Context:
+    """Owns a gf_ctx (scratch memory, cached graphs) on one CUDA device."""
+
+    def __init__(self, device: int = 0):
+        self.device = int(device)
+        h = C.c_void_p()
+        with torch.cuda.device(self.device):
+            check(lib().gf_create(C.byref(h), self.device), "gf_create")
+        self._h = h
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().gf_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # ---------------------------------------------------------------- config
+    def set_launch_config(self, cluster_size: int = 0, n_clusters: int = 0, use_graph: bool = True):
+        check(lib().gf_set_launch_config(self._h, cluster_size, n_clusters, int(use_graph)), "gf_set_launch_config")
+
+    def last_launch(self):
+        a, b = C.c_int(), C.c_int()
+        check(lib().gf_get_last_launch(self._h, C.byref(a), C.byref(b)), "gf_get_last_launch")
+        return a.value, b.value
+
+    def max_active_clusters(self, eps: float, cluster_size: int) -> int:
+        return lib().gf_max_active_clusters(self._h, float(eps), int(cluster_size))
+
+    # ------------------------------------------------------------------ fill
+    def _frame(self, rgba, labels, guide, out, want_enter, want_stall):
+        dev = torch.device("cuda", self.device)
+        rgba = to_rgba(rgba.to(dev))
+        H, W = rgba.shape[:2]
+        labels = labels.to(dev, torch.uint8).contiguous()
+        guide = guide.to(dev, torch.float32).contiguous()
+        if labels.shape != (H, W) or guide.shape != (H, W, 2):
+            raise ValueError("labels must be [H, W] and guide [H, W, 2]")
+        out_rgba = rgba if out == "inplace" else (out if out is not None else torch.empty_like(rgba))
+        shell = torch.empty((H, W), dtype=torch.int32, device=dev)
+        enter = torch.empty((H, W), dtype=torch.int32, device=dev) if want_enter else None
+        stall = torch.empty(((H * W + 1 + 31) // 32,), dtype=torch.int32, device=dev) if want_stall else None
+        fr = _lib.Frame(H, W, rgba.data_ptr(), labels.data_ptr(), guide.data_ptr(), out_rgba.data_ptr(),
+                        shell.data_ptr(), enter.data_ptr() if enter is not None else None,
+                        stall.data_ptr() if stall is not None else None)
+        keep = (rgba, labels, guide)
+        return fr, out_rgba, shell, enter, stall, keep
+
+    def fill(self, rgba, labels, guide, eps=3.0, mu=50.0, c=0.05, ghost=True, smart=True, rescan=False,
+             snap_tau=1e-5, max_shells=0, out=None, enter=False, stall=False, stream=None) -> FillResult:
+        """Fills one frame.  rgba [H,W,3|4] float32, labels [H,W] uint8 (0 known, 1 hole, 2 bystander),
+        guide [H,W,2] float32.  out=None allocates the output, out="inplace" fills rgba in place
+        (rgba must then already be a contiguous [H,W,4] float32 CUDA tensor)."""
+        return self.fill_batched([rgba], [labels], [guide], eps, mu, c, ghost, smart, rescan, snap_tau, max_shells,
+                                 out=None if out is None else [out], enter=enter, stall=stall, stream=stream)[0]
+
+    def fill_batched(self, rgba: Sequence[torch.Tensor], labels: Sequence[torch.Tensor],
+                     guide: Sequence[torch.Tensor], eps=3.0, mu=50.0, c=0.05, ghost=True, smart=True,
+                     rescan=False, snap_tau=1e-5, max_shells=0, out=None, enter=False, stall=False,
+                     stream=None) -> List[FillResult]:
+        n = len(rgba)
+        if not (len(labels) == len(guide) == n) or n == 0:
+            raise ValueError("rgba, labels and guide must have the same non-zero length")
+        outs = out if isinstance(out, (list, tuple)) else [out] * n
+        frames = (_lib.Frame * n)()
+        res, keep = [], []
+        for i in range(n):
+            fr, o, sh, en, st, kp = self._frame(rgba[i], labels[i], guide[i], outs[i], enter, stall)
+            frames[i] = fr
+            keep.append(kp)
+            res.append((o, sh, en, st))
+        stats = torch.empty((n * STATS_BYTES,), dtype=torch.uint8, device=torch.device("cuda", self.device))
+        prm = make_params(eps, mu, c, ghost, smart, rescan, snap_tau, max_shells)
+        with torch.cuda.device(self.device):
+            check(lib().gf_fill_batched(self._h, n, frames, C.byref(prm), _ptr(stats), _stream(stream)),
+                  "gf_fill_batched", self._h)
+        self._keep = keep  # inputs stay alive until the next call on this context
+        return [FillResult(o, sh, en, st, stats[i * STATS_BYTES:(i + 1) * STATS_BYTES])
+                for i, (o, sh, en, st) in enumerate(res)]
+
+    def fill_frames(self, frames, stats: torch.Tensor, params, stream=None, events=None):
+        """Lowest-overhead batched call: ``frames`` is a prepared ctypes array of
+        _lib.Frame, ``stats`` a device buffer of n*48 bytes, ``params`` a _lib.Params;
+        ``events`` an optional pair of recorded torch.cuda.Event placed around the
+        persistent fill kernel."""
+        e0 = C.c_void_p(events[0].cuda_event) if events else None
+        e1 = C.c_void_p(events[1].cuda_event) if events else None
+        check(lib().gf_fill_batched_ex(self._h, len(frames), frames, C.byref(params), _ptr(stats), _stream(stream),
+                                       e0, e1), "gf_fill_batched_ex", self._h)
+
+    # -------------------------------------------------------------- guidance
+    def guidance(self, labels, offsets, pts, eta=3.0, out=None, stream=None) -> torch.Tensor:
+        """Guide field from polylines (Section 3.3), written at hole pixels of ``out``
+        (zero-initialised [H,W,2] float32 when not given)."""
+        return self.guidance_batched([labels], [offsets], [pts], eta, None if out is None else [out], stream)[0]
+
+    def guidance_batched(self, labels, offsets, pts, eta=3.0, out=None, stream=None):
+        dev = torch.device("cuda", self.device)
+        n = len(labels)
+        frames = (_lib.SplineFrame * n)()
+        outs, keep = [], []
+        for i in range(n):
+            lab = labels[i].to(dev, torch.uint8).contiguous()
+            off = torch.as_tensor(offsets[i], dtype=torch.int32).to(dev).contiguous()
+            P = torch.as_tensor(pts[i], dtype=torch.float32).to(dev).contiguous()
+            H, W = lab.shape
+            g = out[i] if out is not None else torch.zeros((H, W, 2), dtype=torch.float32, device=dev)
+            frames[i] = _lib.SplineFrame(H, W, lab.data_ptr(), off.numel() - 1, P.shape[0], off.data_ptr(),
+                                         P.data_ptr(), g.data_ptr())
+            outs.append(g)
+            keep.append((lab, off, P))
+        with torch.cuda.device(self.device):
+            check(lib().gf_guidance_batched(self._h, n, frames, C.c_float(eta), _stream(stream)),
+                  "gf_guidance_batched", self._h)
+        self._gkeep = keep
+        return outs
+
+    # ---------------------------------------------------- host-buffer path
+    def fill_batched_host(self, rgba: Sequence[np.ndarray], labels: Sequence[np.ndarray],
+                          guide: Optional[Sequence[Optional[np.ndarray]]], out_rgba: Sequence[np.ndarray],
+                          out_shell: Sequence[np.ndarray], splines=None, eta=3.0, eps=3.0, mu=50.0, c=0.05,
+                          ghost=True, smart=True, rescan=False, snap_tau=1e-5, max_shells=0,
+                          stream=None) -> np.ndarray:
+        """Fills frames held in HOST memory (numpy; rgba [H,W,4] float32, labels [H,W] uint8,
+        guide [H,W,2] float32 or None with ``splines[i] = (offsets, pts)``); the library
+        copies them to the device, fills, and copies out_rgba / out_shell back.
+        Returns the stats records."""
+        n = len(rgba)
+        Hs = (C.c_int32 * n)(*[a.shape[0] for a in rgba])
+        Ws = (C.c_int32 * n)(*[a.shape[1] for a in rgba])
+
+        def arr(xs):
+            return (C.c_void_p * n)(*[(x.ctypes.data if x is not None else None) for x in xs])
+
+        keep = []
+        if guide is None:
+            guide = [None] * n
+        ns = (C.c_int32 * n)()
+        npts = (C.c_int32 * n)()
+        offs = [None] * n
+        pts = [None] * n
+        if splines is not None:
+            for i, sp in enumerate(splines):
+                if sp is None:
+                    continue
+                o = np.ascontiguousarray(sp[0], np.int32)
+                p = np.ascontiguousarray(sp[1], np.float32)
+                keep += [o, p]
+                offs[i], pts[i] = o, p
+                ns[i] = len(o) - 1
+                npts[i] = p.shape[0]
+        st = np.zeros(n, dtype=STATS_DTYPE)
+        prm = make_params(eps, mu, c, ghost, smart, rescan, snap_tau, max_shells)
+        with torch.cuda.device(self.device):
+            check(lib().gf_fill_batched_host(self._h, n, Hs, Ws, arr(rgba), arr(labels), arr(guide), ns, arr(offs),
+                                             npts, arr(pts), C.c_float(eta), arr(out_rgba), arr(out_shell),
+                                             C.byref(prm), st.ctypes.data, _stream(stream)),
+                  "gf_fill_batched_host", self._h)
+        return st
+
+
+_contexts = {}
+
+
+def context(device: Optional[int] = None) -> Context:
+    d = torch.cuda.current_device() if device is None else int(device)
+    if d not in _contexts:
+        _contexts[d] = Context(d)
+    return _contexts[d]
+
+
+def fill(rgba, labels, guide, **kw) -> FillResult:
+    return context(rgba.device.index if rgba.is_cuda else None).fill(rgba, labels, guide, **kw)
+
+
+def fill_batched(rgba, labels, guide, **kw) -> List[FillResult]:
+    return context().fill_batched(rgba, labels, guide, **kw)
+
+
+def guidance(labels, offsets, pts, eta=3.0, **kw) -> torch.Tensor:
+    return context().guidance(labels, offsets, pts, eta, **kw)

@@ -1,0 +1,110 @@
+"""ctypes binding of libguidefill.so (include/guidefill.h): argument marshalling only.
+
+The shared library is built in-tree by ``paper_1611_05319_gb300.build.build()``.
+If it is missing, loading fails with an error: there is no fallback path.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libguidefill.so")
+
+GF_FLAG_GHOST = 1
+GF_FLAG_SMART = 2
+GF_FLAG_RESCAN = 4
+
+STATUS = {0: "ok", 1: "incomplete", -1: "invalid argument", -2: "CUDA error", -3: "timeout",
+          -4: "no progress", -5: "out of memory", -6: "unsupported device", -7: "internal error"}
+
+# every function declared in include/guidefill.h
+EXPORTS = ["gf_create", "gf_destroy", "gf_status_string", "gf_last_cuda_error", "gf_fill",
+           "gf_fill_batched", "gf_fill_batched_ex", "gf_fill_batched_host", "gf_guidance_from_splines", "gf_guidance_batched",
+           "gf_set_launch_config", "gf_get_last_launch", "gf_max_active_clusters"]
+
+
+class Frame(C.Structure):
+    _fields_ = [("H", C.c_int32), ("W", C.c_int32), ("rgba", C.c_void_p), ("labels", C.c_void_p),
+                ("guide", C.c_void_p), ("out_rgba", C.c_void_p), ("out_shell", C.c_void_p),
+                ("out_enter", C.c_void_p), ("out_stall", C.c_void_p)]
+
+
+class Params(C.Structure):
+    _fields_ = [("eps", C.c_float), ("mu", C.c_float), ("c", C.c_float), ("flags", C.c_uint32),
+                ("snap_tau", C.c_float), ("max_shells", C.c_int32)]
+
+
+class SplineFrame(C.Structure):
+    _fields_ = [("H", C.c_int32), ("W", C.c_int32), ("labels", C.c_void_p), ("n_splines", C.c_int32),
+                ("n_points", C.c_int32), ("offsets", C.c_void_p), ("pts", C.c_void_p), ("guide", C.c_void_p)]
+
+
+STATS_DTYPE = np.dtype([("shells", np.int32), ("stalls", np.int32), ("status", np.int32), ("reserved", np.int32),
+                        ("filled", np.int64), ("evaluations", np.int64), ("max_front", np.int64),
+                        ("holes", np.int64)])
+STATS_BYTES = STATS_DTYPE.itemsize  # 48
+
+
+class GuidefillError(RuntimeError):
+    def __init__(self, code, what=""):
+        super().__init__(f"{what}: {STATUS.get(code, code)} ({code})")
+        self.code = code
+
+
+_lib = None
+
+
+def lib() -> C.CDLL:
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: build it with paper_1611_05319_gb300.build.build() "
+                               "(requires nvcc); there is no CPU fallback")
+        L = C.CDLL(LIB_PATH)
+        P = C.c_void_p
+        L.gf_create.argtypes = [C.POINTER(P), C.c_int]
+        L.gf_create.restype = C.c_int
+        L.gf_destroy.argtypes = [P]
+        L.gf_destroy.restype = None
+        L.gf_status_string.argtypes = [C.c_int]
+        L.gf_status_string.restype = C.c_char_p
+        L.gf_last_cuda_error.argtypes = [P]
+        L.gf_last_cuda_error.restype = C.c_int
+        L.gf_fill.argtypes = [P, C.POINTER(Frame), C.POINTER(Params), P, P]
+        L.gf_fill.restype = C.c_int
+        L.gf_fill_batched.argtypes = [P, C.c_int, C.POINTER(Frame), C.POINTER(Params), P, P]
+        L.gf_fill_batched.restype = C.c_int
+        L.gf_fill_batched_ex.argtypes = [P, C.c_int, C.POINTER(Frame), C.POINTER(Params), P, P, P, P]
+        L.gf_fill_batched_ex.restype = C.c_int
+        L.gf_fill_batched_host.argtypes = [P, C.c_int, P, P, P, P, P, P, P, P, P, C.c_float, P, P,
+                                           C.POINTER(Params), P, P]
+        L.gf_fill_batched_host.restype = C.c_int
+        L.gf_guidance_from_splines.argtypes = [P, C.c_int, C.c_int, P, C.c_int, P, C.c_int, P, C.c_float, P, P]
+        L.gf_guidance_from_splines.restype = C.c_int
+        L.gf_guidance_batched.argtypes = [P, C.c_int, C.POINTER(SplineFrame), C.c_float, P]
+        L.gf_guidance_batched.restype = C.c_int
+        L.gf_set_launch_config.argtypes = [P, C.c_int, C.c_int, C.c_int]
+        L.gf_set_launch_config.restype = C.c_int
+        L.gf_get_last_launch.argtypes = [P, C.POINTER(C.c_int), C.POINTER(C.c_int)]
+        L.gf_get_last_launch.restype = C.c_int
+        L.gf_max_active_clusters.argtypes = [P, C.c_float, C.c_int]
+        L.gf_max_active_clusters.restype = C.c_int
+        _lib = L
+    return _lib
+
+
+def check(code: int, what: str, ctx=None):
+    if code < 0:
+        extra = ""
+        if ctx is not None and code == -2:
+            extra = f" (cudaError {lib().gf_last_cuda_error(ctx)})"
+        raise GuidefillError(code, what + extra)
+    return code
+
+
+def make_params(eps=3.0, mu=50.0, c=0.05, ghost=True, smart=True, rescan=False, snap_tau=1e-5, max_shells=0):
+    flags = (GF_FLAG_GHOST if ghost else 0) | (GF_FLAG_SMART if smart else 0) | (GF_FLAG_RESCAN if rescan else 0)
+    return Params(float(eps), float(mu), float(c), flags, float(snap_tau), int(max_shells))

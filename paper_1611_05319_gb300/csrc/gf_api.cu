@@ -1,0 +1,721 @@
+// Host side of the Guidefill C ABI (include/guidefill.h).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdint>
+#include <cstdio>
+#include <cstring>
+#include <vector>
+
+#include "gf_internal.cuh"
+
+
+using namespace gf;
+
+struct DevBuf {
+    void *ptr = nullptr;
+    size_t bytes = 0;
+};
+
+struct gf_ctx {
+    int device = 0;
+    int sm_count = 0;
+    int last_cuda = 0;
+    DevBuf arena;       // fill scratch
+    DevBuf garena;      // guidance scratch
+    DevBuf io;          // host-buffer path device copies
+    // cached graphs of the last batched fill: gexec = preparation (descriptor
+    // upload, clears, init, frame order), gexec_fill = the persistent fill kernel
+    cudaGraphExec_t gexec = nullptr;
+    cudaGraphExec_t gexec_fill = nullptr;
+    uint64_t gkey = 0;
+    // launch configuration (0 = automatic)
+    int cluster_size = 0;
+    int n_clusters = 0;
+    int use_graph = 1;
+    int last_cluster_size = 0, last_n_clusters = 0;
+};
+
+static gf_status cuda_fail(gf_ctx *ctx, cudaError_t e)
+{
+    if (ctx) ctx->last_cuda = (int)e;
+    return e == cudaErrorMemoryAllocation ? GF_ERR_OOM : GF_ERR_CUDA;
+}
+#define CK(call)                                   \
+    do {                                           \
+        cudaError_t e_ = (call);                   \
+        if (e_ != cudaSuccess) return cuda_fail(ctx, e_); \
+    } while (0)
+
+static void drop_graphs(gf_ctx *ctx, cudaStream_t stream)
+{
+    if (stream) cudaStreamSynchronize(stream);
+    if (ctx->gexec) cudaGraphExecDestroy(ctx->gexec);
+    if (ctx->gexec_fill) cudaGraphExecDestroy(ctx->gexec_fill);
+    ctx->gexec = nullptr;
+    ctx->gexec_fill = nullptr;
+    ctx->gkey = 0;
+}
+
+static gf_status ensure(gf_ctx *ctx, DevBuf &b, size_t bytes)
+{
+    if (b.bytes >= bytes) return GF_OK;
+    if (b.ptr) {
+        cudaError_t e = cudaDeviceSynchronize();
+        if (e != cudaSuccess) return cuda_fail(ctx, e);
+        cudaFree(b.ptr);
+        b.ptr = nullptr;
+        b.bytes = 0;
+        drop_graphs(ctx, nullptr);
+    }
+    size_t nb = std::max(bytes, (size_t)1 << 20);
+    nb = (nb + ((size_t)1 << 20) - 1) & ~(((size_t)1 << 20) - 1);
+    cudaError_t e = cudaMalloc(&b.ptr, nb);
+    if (e != cudaSuccess) return cuda_fail(ctx, e);
+    b.bytes = nb;
+    return GF_OK;
+}
+
+static inline size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
+static void build_tab(float eps, SampleTab &tab)
+{
+    memset(&tab, 0, sizeof(tab));
+    const double e = (double)eps;
+    const int R = (int)std::ceil(e);
+    std::vector<int> cn, cm;
+    for (int m = -R; m <= R; m++)
+        for (int n = -R; n <= R; n++) {
+            if (n == 0 && m == 0) continue;
+            if ((double)(n * n + m * m) <= e * e) {
+                cn.push_back(n);
+                cm.push_back(m);
+            }
+        }
+    tab.ns = (int)cn.size();
+    tab.R = R;
+    for (int s = 0; s < tab.ns; s++) {
+        tab.cn[s] = (int8_t)cn[s];
+        tab.cm[s] = (int8_t)cm[s];
+    }
+    int pos = 0;
+    for (int g = 0; g <= R; g++) {
+        tab.m_start[g] = pos;
+        float D = 0.f;
+        for (int s = 0; s < tab.ns; s++) {
+            if (std::abs(cm[s]) != g) continue;
+            float inv = (float)(1.0 / std::sqrt((double)(cn[s] * cn[s] + cm[s] * cm[s])));
+            tab.n_f[pos] = (float)cn[s];
+            tab.m_f[pos] = (float)cm[s];
+            tab.invd[pos] = inv;
+            D += inv;
+            pos++;
+        }
+        tab.Dm[g] = D;
+    }
+    for (int g = R + 1; g <= MAX_R + 1; g++) tab.m_start[g] = pos;
+}
+
+static uint64_t fnv(uint64_t h, const void *p, size_t n)
+{
+    const unsigned char *c = (const unsigned char *)p;
+    for (size_t i = 0; i < n; i++) {
+        h ^= c[i];
+        h *= 1099511628211ull;
+    }
+    return h;
+}
+
+static int rw_for(float eps)
+{
+    int R = (int)std::ceil((double)eps);
+    return R <= 3 ? 4 : (R == 4 ? 5 : 8);
+}
+
+static size_t warp_smem(int rw)
+{
+    int ws = 8 + 2 * rw;
+    size_t b = (size_t)ws * ws * 16 + (size_t)ws * 4 + 64 * 4 + 8;
+    return align_up(b, 16);
+}
+
+static const void *fill_kernel_ptr(int rw) { return fill_kernel_entry(rw); }
+
+static gf_status check_params(const gf_params *p)
+{
+    if (!p) return GF_ERR_ARG;
+    if (!(p->eps >= 1.0f && p->eps <= 7.0f)) return GF_ERR_ARG;
+    if (!(p->mu >= 0.0f) || !std::isfinite(p->mu)) return GF_ERR_ARG;
+    if (p->flags & ~(GF_FLAG_GHOST | GF_FLAG_SMART | GF_FLAG_RESCAN)) return GF_ERR_ARG;
+    if ((p->flags & GF_FLAG_SMART) && !(p->c >= 1e-6f && p->c < 1.0f)) return GF_ERR_ARG;
+    if (!(p->snap_tau >= 0.0f && p->snap_tau < 0.01f)) return GF_ERR_ARG;
+    if (p->max_shells < 0) return GF_ERR_ARG;
+    return GF_OK;
+}
+
+static gf_status check_frame(const gf_frame *f)
+{
+    if (!f) return GF_ERR_ARG;
+    if (f->H <= 0 || f->W <= 0) return GF_ERR_ARG;
+    if ((int64_t)f->H * f->W > ((int64_t)1 << 31) - 64) return GF_ERR_ARG;
+    if (!f->rgba || !f->labels || !f->guide || !f->out_rgba || !f->out_shell) return GF_ERR_ARG;
+    if (((uintptr_t)f->rgba & 15) || ((uintptr_t)f->out_rgba & 15)) return GF_ERR_ARG;
+    if (((uintptr_t)f->guide & 7) || ((uintptr_t)f->out_shell & 3)) return GF_ERR_ARG;
+    if (f->out_enter && ((uintptr_t)f->out_enter & 3)) return GF_ERR_ARG;
+    if (f->out_stall && ((uintptr_t)f->out_stall & 3)) return GF_ERR_ARG;
+    return GF_OK;
+}
+
+extern "C" {
+
+const char *gf_status_string(int s)
+{
+    switch (s) {
+    case GF_OK: return "ok";
+    case GF_INCOMPLETE: return "incomplete: some hole pixels could not be reached";
+    case GF_ERR_ARG: return "invalid argument";
+    case GF_ERR_CUDA: return "CUDA error";
+    case GF_ERR_TIMEOUT: return "device wait timed out";
+    case GF_ERR_NO_PROGRESS: return "shell loop reached max_shells";
+    case GF_ERR_OOM: return "out of device memory";
+    case GF_ERR_UNSUPPORTED: return "unsupported device";
+    case GF_ERR_INTERNAL: return "internal consistency check failed";
+    default: return "unknown status";
+    }
+}
+
+int gf_last_cuda_error(const gf_ctx *ctx) { return ctx ? ctx->last_cuda : 0; }
+
+gf_status gf_create(gf_ctx **out, int device)
+{
+    if (!out) return GF_ERR_ARG;
+    *out = nullptr;
+    gf_ctx *ctx = nullptr;
+    int ndev = 0;
+    cudaError_t e = cudaGetDeviceCount(&ndev);
+    if (e != cudaSuccess) return GF_ERR_CUDA;
+    if (device < 0 || device >= ndev) return GF_ERR_ARG;
+    cudaDeviceProp prop;
+    e = cudaGetDeviceProperties(&prop, device);
+    if (e != cudaSuccess) return GF_ERR_CUDA;
+    if (!(prop.major == 10 && prop.minor == 3)) return GF_ERR_UNSUPPORTED;
+    e = cudaSetDevice(device);
+    if (e != cudaSuccess) return GF_ERR_CUDA;
+    ctx = new gf_ctx();
+    ctx->device = device;
+    ctx->sm_count = prop.multiProcessorCount;
+    for (int rw : {4, 5, 8}) {
+        const void *k = fill_kernel_ptr(rw);
+        size_t smem = warp_smem(rw) * WARPS_PER_CTA;
+        e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e == cudaSuccess) e = cudaFuncSetAttribute(k, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+        if (e != cudaSuccess) {
+            ctx->last_cuda = (int)e;
+            delete ctx;
+            return GF_ERR_CUDA;
+        }
+    }
+    *out = ctx;
+    return GF_OK;
+}
+
+void gf_destroy(gf_ctx *ctx)
+{
+    if (!ctx) return;
+    cudaSetDevice(ctx->device);
+    cudaDeviceSynchronize();
+    drop_graphs(ctx, nullptr);
+    if (ctx->arena.ptr) cudaFree(ctx->arena.ptr);
+    if (ctx->garena.ptr) cudaFree(ctx->garena.ptr);
+    if (ctx->io.ptr) cudaFree(ctx->io.ptr);
+    delete ctx;
+}
+
+/* Launch shape of the persistent fill (0 = automatic).  Used by the autotuner
+ * and by tests that check results do not depend on the launch shape. */
+gf_status gf_set_launch_config(gf_ctx *ctx, int cluster_size, int n_clusters, int use_graph)
+{
+    if (!ctx) return GF_ERR_ARG;
+    if (cluster_size != 0 && cluster_size != 1 && cluster_size != 2 && cluster_size != 4 &&
+        cluster_size != 8 && cluster_size != 16)
+        return GF_ERR_ARG;
+    if (n_clusters < 0) return GF_ERR_ARG;
+    ctx->cluster_size = cluster_size;
+    ctx->n_clusters = n_clusters;
+    ctx->use_graph = use_graph ? 1 : 0;
+    return GF_OK;
+}
+
+/* Launch shape used by the last fill call. */
+gf_status gf_get_last_launch(const gf_ctx *ctx, int *cluster_size, int *n_clusters)
+{
+    if (!ctx || !cluster_size || !n_clusters) return GF_ERR_ARG;
+    *cluster_size = ctx->last_cluster_size;
+    *n_clusters = ctx->last_n_clusters;
+    return GF_OK;
+}
+
+/* Maximum number of co-resident clusters of the given size for eps. */
+int gf_max_active_clusters(gf_ctx *ctx, float eps, int cluster_size)
+{
+    if (!ctx) return -1;
+    int rw = rw_for(eps);
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(cluster_size * 64);
+    cfg.blockDim = dim3(CTA_THREADS);
+    cfg.dynamicSmemBytes = warp_smem(rw) * WARPS_PER_CTA;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = cluster_size;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    int n = 0;
+    cudaError_t e = cudaOccupancyMaxActiveClusters(&n, fill_kernel_ptr(rw), &cfg);
+    if (e != cudaSuccess) {
+        ctx->last_cuda = (int)e;
+        cudaGetLastError();
+        return 0;
+    }
+    return n;
+}
+
+static gf_status enqueue_fill(gf_ctx *ctx, int n, const gf_frame *frames, const gf_params *prm,
+                              gf_stats *dev_stats, cudaStream_t stream, cudaEvent_t ev0 = nullptr,
+                              cudaEvent_t ev1 = nullptr)
+{
+    // ---- layout of the scratch arena
+    std::vector<size_t> off_U(n), off_Q(n), off_F(n), off_S(n);
+    std::vector<int> ntiles(n);
+    size_t pos = 0;
+    int list_cap = 1;
+    for (int i = 0; i < n; i++) {
+        int TW = (frames[i].W + 7) / 8, TH = (frames[i].H + 7) / 8;
+        ntiles[i] = TW * TH;
+        list_cap = std::max(list_cap, ntiles[i]);
+        off_U[i] = pos; pos = align_up(pos + 8 * (size_t)ntiles[i], 256);
+        off_Q[i] = pos; pos = align_up(pos + 8 * (size_t)ntiles[i], 256);
+        off_F[i] = pos; pos = align_up(pos + sizeof(TileF) * 2 * (size_t)ntiles[i], 256);
+        off_S[i] = pos; pos = align_up(pos + 4 * (size_t)ntiles[i], 256);
+    }
+    const size_t off_holes = pos; pos = align_up(pos + 4 * (size_t)n, 256);
+    const size_t off_desc = pos; pos = align_up(pos + sizeof(FrameDev) * (size_t)n, 256);
+    const size_t off_order = pos; pos = align_up(pos + 4 * (size_t)n, 256);
+    const size_t off_cursor = pos; pos = align_up(pos + 4, 256);
+    const size_t off_ctaoff = pos; pos = align_up(pos + 4 * (size_t)(n + 1), 256);
+
+    // ---- launch shape
+    const int rw = rw_for(prm->eps);
+    int cs = ctx->cluster_size;
+    if (cs == 0) cs = (n == 1) ? 16 : 2;
+    int maxc = gf_max_active_clusters(ctx, prm->eps, cs);
+    while (maxc <= 0 && cs > 1) {
+        cs /= 2;
+        maxc = gf_max_active_clusters(ctx, prm->eps, cs);
+    }
+    if (maxc <= 0) return GF_ERR_UNSUPPORTED;
+    int nc = ctx->n_clusters > 0 ? std::min(ctx->n_clusters, maxc) : maxc;
+    nc = std::max(1, std::min(nc, n));
+    ctx->last_cluster_size = cs;
+    ctx->last_n_clusters = nc;
+
+    const size_t off_ctl = pos; pos = align_up(pos + sizeof(GroupCtl) * (size_t)nc, 256);
+    const size_t off_lists = pos; pos = align_up(pos + 4 * (size_t)3 * list_cap * nc, 256);
+    gf_status st = ensure(ctx, ctx->arena, pos);
+    if (st != GF_OK) return st;
+    char *A = (char *)ctx->arena.ptr;
+
+    // ---- frame descriptors (uploaded by value through kernel parameters)
+    std::vector<FrameDev> hdv(n);
+    std::vector<int32_t> hctav(n + 1);
+    FrameDev *hd = hdv.data();
+    int32_t *hcta = hctav.data();
+    int64_t ctas = 0;
+    for (int i = 0; i < n; i++) {
+        const gf_frame &f = frames[i];
+        FrameDev d;
+        memset(&d, 0, sizeof(d));
+        d.H = f.H;
+        d.W = f.W;
+        d.TW = (f.W + 7) / 8;
+        d.TH = (f.H + 7) / 8;
+        d.ntiles = ntiles[i];
+        const int64_t full = (int64_t)f.H * f.W + 1;
+        int64_t cap = prm->max_shells > 0 ? std::min<int64_t>(prm->max_shells, full) : full;
+        d.max_shells = (int32_t)std::min<int64_t>(cap, INT32_MAX - 2);
+        d.rgba = (float4 *)f.out_rgba;
+        d.labels = f.labels;
+        d.guide = (const float2 *)f.guide;
+        d.shell = f.out_shell;
+        d.enter = f.out_enter;
+        d.stall_bits = f.out_stall;
+        d.stats = dev_stats + i;
+        d.U = (unsigned long long *)(A + off_U[i]);
+        d.Qw = (unsigned long long *)(A + off_Q[i]);
+        d.F = (TileF *)(A + off_F[i]);
+        d.sched = (int32_t *)(A + off_S[i]);
+        d.holes = (int32_t *)(A + off_holes) + i;
+        hd[i] = d;
+        hcta[i] = (int32_t)ctas;
+        ctas += (int64_t)d.TH * ((f.W + 255) / 256);
+    }
+    hcta[n] = (int32_t)ctas;
+    if (ctas >= INT32_MAX) return GF_ERR_ARG;
+
+    FillParams fp;
+    memset(&fp, 0, sizeof(fp));
+    fp.eps = prm->eps;
+    fp.mu = prm->mu;
+    fp.c = prm->c;
+    fp.tau = prm->snap_tau;
+    fp.coef32 = (prm->mu * prm->mu) / (2.0f * prm->eps * prm->eps);
+    fp.coef64 = (double)prm->mu * (double)prm->mu / (2.0 * (double)prm->eps * (double)prm->eps);
+    fp.c64 = (double)prm->c;
+    fp.flags = prm->flags;
+    fp.n_frames = n;
+    fp.list_cap = list_cap;
+    fp.frames = (FrameDev *)(A + off_desc);
+    fp.frame_order = (int32_t *)(A + off_order);
+    fp.frame_cursor = (int32_t *)(A + off_cursor);
+    fp.groups = (GroupCtl *)(A + off_ctl);
+    fp.lists = (int32_t *)(A + off_lists);
+    build_tab(prm->eps, fp.tab);
+
+    // graph key: everything the enqueued work depends on
+    uint64_t key = 1469598103934665603ull;
+    key = fnv(key, hd, sizeof(FrameDev) * (size_t)n);
+    key = fnv(key, prm, sizeof(*prm));
+    key = fnv(key, &cs, sizeof(cs));
+    key = fnv(key, &nc, sizeof(nc));
+    key = fnv(key, &n, sizeof(n));
+    for (int i = 0; i < n; i++) key = fnv(key, &frames[i].rgba, sizeof(void *));
+    key = fnv(key, &ctx->arena.ptr, sizeof(void *));
+
+    const bool graph = ctx->use_graph && stream != nullptr;
+    if (graph && ctx->gexec && ctx->gexec_fill && ctx->gkey == key) {
+        CK(cudaGraphLaunch(ctx->gexec, stream));
+        if (ev0) CK(cudaEventRecord(ev0, stream));
+        CK(cudaGraphLaunch(ctx->gexec_fill, stream));
+        if (ev1) CK(cudaEventRecord(ev1, stream));
+        return GF_OK;
+    }
+    if (graph && (ctx->gexec || ctx->gexec_fill)) drop_graphs(ctx, stream);
+
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)(nc * cs));
+    cfg.blockDim = dim3(CTA_THREADS);
+    cfg.dynamicSmemBytes = warp_smem(rw) * WARPS_PER_CTA;
+    cfg.stream = stream;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = cs;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+
+    // ---- phase 1: descriptors, clears, init, frame order
+    if (graph) CK(cudaStreamBeginCapture(stream, cudaStreamCaptureModeThreadLocal));
+    cudaError_t e = cudaSuccess;
+    do {
+        for (int c0 = 0; c0 < n && !e; c0 += DESC_CHUNK) {
+            static thread_local FrameChunk ch;  // large: keep off the stack
+            ch.dst_frames = (FrameDev *)(A + off_desc);
+            ch.dst_cta = (int32_t *)(A + off_ctaoff);
+            ch.first = c0;
+            ch.count = std::min(DESC_CHUNK, n - c0);
+            ch.last_chunk = (c0 + ch.count == n) ? 1 : 0;
+            for (int i = 0; i < ch.count; i++) {
+                ch.frames[i] = hd[c0 + i];
+                ch.cta[i] = hcta[c0 + i];
+            }
+            ch.cta[ch.count] = hcta[c0 + ch.count];
+            upload_frames_kernel<<<1, 128, 0, stream>>>(ch);
+            e = cudaGetLastError();
+        }
+        if (e) break;
+        e = cudaMemsetAsync(A + off_holes, 0, 4 * (size_t)n, stream);
+        if (e) break;
+        e = cudaMemsetAsync(A + off_ctl, 0, sizeof(GroupCtl) * (size_t)nc, stream);
+        if (e) break;
+        for (int i = 0; i < n && !e; i++) {
+            const gf_frame &f = frames[i];
+            if (f.out_rgba != f.rgba)
+                e = cudaMemcpyAsync(f.out_rgba, f.rgba, (size_t)f.H * f.W * 16, cudaMemcpyDeviceToDevice, stream);
+            if (!e && f.out_stall)
+                e = cudaMemsetAsync(f.out_stall, 0, 4 * (((size_t)f.H * f.W + 1 + 31) / 32), stream);
+        }
+        if (e) break;
+        InitArgs ia;
+        ia.frames = fp.frames;
+        ia.cta_offset = (const int32_t *)(A + off_ctaoff);
+        ia.n_frames = n;
+        init_kernel<<<(unsigned)ctas, 256, 0, stream>>>(ia);
+        e = cudaGetLastError();
+        if (e) break;
+        order_kernel<<<1, 256, 0, stream>>>(fp.frames, n, fp.frame_order, fp.frame_cursor);
+        e = cudaGetLastError();
+    } while (0);
+    cudaGraph_t g1 = nullptr;
+    if (graph) {
+        cudaError_t e2 = cudaStreamEndCapture(stream, &g1);
+        if (e == cudaSuccess) e = e2;
+    }
+    if (e != cudaSuccess) {
+        if (g1) cudaGraphDestroy(g1);
+        return cuda_fail(ctx, e);
+    }
+    if (!graph) {
+        // ---- phase 2 directly
+        if (ev0) CK(cudaEventRecord(ev0, stream));
+        CK(launch_fill(rw, cfg, fp));
+        if (ev1) CK(cudaEventRecord(ev1, stream));
+        return GF_OK;
+    }
+    // ---- phase 2 captured separately so that timing events can sit between the two graphs
+    cudaGraph_t g2 = nullptr;
+    e = cudaStreamBeginCapture(stream, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+        e = launch_fill(rw, cfg, fp);
+        cudaError_t e2 = cudaStreamEndCapture(stream, &g2);
+        if (e == cudaSuccess) e = e2;
+    }
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&ctx->gexec, g1, 0);
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&ctx->gexec_fill, g2, 0);
+    if (g1) cudaGraphDestroy(g1);
+    if (g2) cudaGraphDestroy(g2);
+    if (e != cudaSuccess) {
+        drop_graphs(ctx, nullptr);
+        return cuda_fail(ctx, e);
+    }
+    ctx->gkey = key;
+    CK(cudaGraphLaunch(ctx->gexec, stream));
+    if (ev0) CK(cudaEventRecord(ev0, stream));
+    CK(cudaGraphLaunch(ctx->gexec_fill, stream));
+    if (ev1) CK(cudaEventRecord(ev1, stream));
+    return GF_OK;
+}
+
+gf_status gf_fill_batched_ex(gf_ctx *ctx, int n, const gf_frame *frames, const gf_params *params,
+                             gf_stats *dev_stats, void *stream, void *event_fill_start, void *event_fill_end)
+{
+    if (!ctx || n <= 0 || !frames || !dev_stats) return GF_ERR_ARG;
+    gf_status s = check_params(params);
+    if (s != GF_OK) return s;
+    for (int i = 0; i < n; i++) {
+        s = check_frame(&frames[i]);
+        if (s != GF_OK) return s;
+    }
+    cudaError_t e = cudaSetDevice(ctx->device);
+    if (e != cudaSuccess) return cuda_fail(ctx, e);
+    return enqueue_fill(ctx, n, frames, params, dev_stats, (cudaStream_t)stream, (cudaEvent_t)event_fill_start,
+                        (cudaEvent_t)event_fill_end);
+}
+
+gf_status gf_fill_batched(gf_ctx *ctx, int n, const gf_frame *frames, const gf_params *params,
+                          gf_stats *dev_stats, void *stream)
+{
+    return gf_fill_batched_ex(ctx, n, frames, params, dev_stats, stream, nullptr, nullptr);
+}
+
+gf_status gf_fill(gf_ctx *ctx, const gf_frame *frame, const gf_params *params, gf_stats *dev_stats,
+                  void *stream)
+{
+    return gf_fill_batched(ctx, 1, frame, params, dev_stats, stream);
+}
+
+gf_status gf_guidance_batched(gf_ctx *ctx, int n, const gf_spline_frame *frames, float eta, void *stream)
+{
+    if (!ctx || n <= 0 || !frames || !(eta > 0.0f) || !std::isfinite(eta)) return GF_ERR_ARG;
+    for (int i = 0; i < n; i++) {
+        const gf_spline_frame &f = frames[i];
+        if (f.H <= 0 || f.W <= 0 || !f.labels || !f.guide || f.n_splines < 0 || f.n_points < 0) return GF_ERR_ARG;
+        if ((int64_t)f.H * f.W > ((int64_t)1 << 31) - 64) return GF_ERR_ARG;
+        if (f.n_splines > 0 && (!f.offsets || !f.pts)) return GF_ERR_ARG;
+        if (((uintptr_t)f.guide & 7) || (f.pts && ((uintptr_t)f.pts & 7))) return GF_ERR_ARG;
+    }
+    cudaError_t e = cudaSetDevice(ctx->device);
+    if (e != cudaSuccess) return cuda_fail(ctx, e);
+    cudaStream_t st = (cudaStream_t)stream;
+    std::vector<size_t> off_cnt(n), off_list(n);
+    size_t pos = 0;
+    int64_t tot_pts = 0, tot_bins = 0;
+    for (int i = 0; i < n; i++) {
+        int NBX = (frames[i].W + BIN - 1) / BIN, NBY = (frames[i].H + BIN - 1) / BIN;
+        off_cnt[i] = pos; pos = align_up(pos + 4 * (size_t)NBX * NBY, 256);
+        off_list[i] = pos; pos = align_up(pos + 4 * (size_t)NBX * NBY * BIN_CAP, 256);
+        tot_pts += frames[i].n_points;
+        tot_bins += (int64_t)NBX * NBY;
+    }
+    if (tot_pts >= INT32_MAX || tot_bins >= INT32_MAX) return GF_ERR_ARG;
+    const size_t off_desc = pos; pos = align_up(pos + sizeof(SplineFrameDev) * (size_t)n, 256);
+    const size_t off_po = pos; pos = align_up(pos + 4 * (size_t)(n + 1), 256);
+    const size_t off_bo = pos; pos = align_up(pos + 4 * (size_t)(n + 1), 256);
+    gf_status s = ensure(ctx, ctx->garena, pos);
+    if (s != GF_OK) return s;
+    char *A = (char *)ctx->garena.ptr;
+    std::vector<SplineFrameDev> hdv(n);
+    std::vector<int32_t> hpov(n + 1), hbov(n + 1);
+    SplineFrameDev *hd = hdv.data();
+    int32_t *hpo = hpov.data();
+    int32_t *hbo = hbov.data();
+    int64_t pp = 0, bb = 0;
+    for (int i = 0; i < n; i++) {
+        const gf_spline_frame &f = frames[i];
+        SplineFrameDev d;
+        d.H = f.H; d.W = f.W;
+        d.NBX = (f.W + BIN - 1) / BIN; d.NBY = (f.H + BIN - 1) / BIN;
+        d.n_splines = f.n_splines; d.n_points = f.n_points;
+        d.labels = f.labels; d.offsets = f.offsets; d.pts = (const float2 *)f.pts;
+        d.guide = (float2 *)f.guide;
+        d.bin_count = (int32_t *)(A + off_cnt[i]);
+        d.bin_list = (int32_t *)(A + off_list[i]);
+        hd[i] = d;
+        hpo[i] = (int32_t)pp; hbo[i] = (int32_t)bb;
+        pp += f.n_points;
+        bb += (int64_t)d.NBX * d.NBY;
+    }
+    hpo[n] = (int32_t)pp; hbo[n] = (int32_t)bb;
+    // counts must be zero; lists need no clearing
+    for (int i = 0; i < n; i++) {
+        size_t nbins = (size_t)hd[i].NBX * hd[i].NBY;
+        CK(cudaMemsetAsync(A + off_cnt[i], 0, 4 * nbins, st));
+    }
+    for (int c0 = 0; c0 < n; c0 += DESC_CHUNK) {
+        static thread_local SplineChunk ch;
+        ch.dst_frames = (SplineFrameDev *)(A + off_desc);
+        ch.dst_po = (int32_t *)(A + off_po);
+        ch.dst_bo = (int32_t *)(A + off_bo);
+        ch.first = c0;
+        ch.count = std::min(DESC_CHUNK, n - c0);
+        ch.last_chunk = (c0 + ch.count == n) ? 1 : 0;
+        for (int i = 0; i < ch.count; i++) {
+            ch.frames[i] = hd[c0 + i];
+            ch.po[i] = hpo[c0 + i];
+            ch.bo[i] = hbo[c0 + i];
+        }
+        ch.po[ch.count] = hpo[c0 + ch.count];
+        ch.bo[ch.count] = hbo[c0 + ch.count];
+        upload_splines_kernel<<<1, 128, 0, st>>>(ch);
+        CK(cudaGetLastError());
+    }
+    GuideArgs ga;
+    ga.frames = (const SplineFrameDev *)(A + off_desc);
+    ga.point_offset = (const int32_t *)(A + off_po);
+    ga.bin_offset = (const int32_t *)(A + off_bo);
+    ga.n_frames = n;
+    ga.eta = eta;
+    if (pp > 0) {
+        bin_kernel<<<(unsigned)((pp + 255) / 256), 256, 0, st>>>(ga, (int)pp);
+        CK(cudaGetLastError());
+    }
+    guide_kernel<<<(unsigned)bb, 256, 0, st>>>(ga);
+    CK(cudaGetLastError());
+    return GF_OK;
+}
+
+gf_status gf_guidance_from_splines(gf_ctx *ctx, int H, int W, const uint8_t *labels, int n_splines,
+                                   const int32_t *offsets, int n_points, const float *pts, float eta,
+                                   float *guide, void *stream)
+{
+    gf_spline_frame f;
+    f.H = H; f.W = W; f.labels = labels; f.n_splines = n_splines; f.n_points = n_points;
+    f.offsets = offsets; f.pts = pts; f.guide = guide;
+    return gf_guidance_batched(ctx, 1, &f, eta, stream);
+}
+
+gf_status gf_fill_batched_host(gf_ctx *ctx, int n, const int32_t *H, const int32_t *W,
+                               const float *const *host_rgba, const uint8_t *const *host_labels,
+                               const float *const *host_guide, const int32_t *n_splines,
+                               const int32_t *const *host_offsets, const int32_t *n_points,
+                               const float *const *host_pts, float eta, float *const *host_out_rgba,
+                               int32_t *const *host_out_shell, const gf_params *params,
+                               gf_stats *host_stats, void *stream)
+{
+    if (!ctx || n <= 0 || !H || !W || !host_rgba || !host_labels || !host_out_rgba || !host_out_shell ||
+        !host_stats)
+        return GF_ERR_ARG;
+    gf_status s = check_params(params);
+    if (s != GF_OK) return s;
+    std::vector<size_t> o_rgba(n), o_lab(n), o_g(n), o_sh(n), o_off(n), o_pts(n);
+    std::vector<char> from_splines(n, 0);
+    size_t pos = 0;
+    for (int i = 0; i < n; i++) {
+        if (H[i] <= 0 || W[i] <= 0 || !host_rgba[i] || !host_labels[i] || !host_out_rgba[i] || !host_out_shell[i])
+            return GF_ERR_ARG;
+        if ((int64_t)H[i] * W[i] > ((int64_t)1 << 31) - 64) return GF_ERR_ARG;
+        from_splines[i] = (!host_guide || !host_guide[i]) ? 1 : 0;
+        if (from_splines[i]) {
+            if (!n_splines || !n_points || !host_offsets || !host_pts || n_splines[i] < 0 || n_points[i] < 0)
+                return GF_ERR_ARG;
+            if (n_splines[i] > 0 && (!host_offsets[i] || !host_pts[i])) return GF_ERR_ARG;
+            if (!(eta > 0.0f) || !std::isfinite(eta)) return GF_ERR_ARG;
+        }
+        size_t np = (size_t)H[i] * W[i];
+        o_rgba[i] = pos; pos = align_up(pos + 16 * np, 256);
+        o_lab[i] = pos; pos = align_up(pos + np, 256);
+        o_g[i] = pos; pos = align_up(pos + 8 * np, 256);
+        o_sh[i] = pos; pos = align_up(pos + 4 * np, 256);
+        o_off[i] = pos; pos = align_up(pos + (from_splines[i] ? 4 * (size_t)(n_splines[i] + 1) : 0), 256);
+        o_pts[i] = pos; pos = align_up(pos + (from_splines[i] ? 8 * (size_t)n_points[i] : 0), 256);
+    }
+    const size_t o_st = pos; pos = align_up(pos + sizeof(gf_stats) * (size_t)n, 256);
+    cudaError_t e = cudaSetDevice(ctx->device);
+    if (e != cudaSuccess) return cuda_fail(ctx, e);
+    s = ensure(ctx, ctx->io, pos);
+    if (s != GF_OK) return s;
+    char *A = (char *)ctx->io.ptr;
+    cudaStream_t st = (cudaStream_t)stream;
+    std::vector<gf_frame> fr(n);
+    std::vector<gf_spline_frame> sf;
+    for (int i = 0; i < n; i++) {
+        size_t np = (size_t)H[i] * W[i];
+        CK(cudaMemcpyAsync(A + o_rgba[i], host_rgba[i], 16 * np, cudaMemcpyHostToDevice, st));
+        CK(cudaMemcpyAsync(A + o_lab[i], host_labels[i], np, cudaMemcpyHostToDevice, st));
+        if (!from_splines[i]) {
+            CK(cudaMemcpyAsync(A + o_g[i], host_guide[i], 8 * np, cudaMemcpyHostToDevice, st));
+        } else {
+            if (n_splines[i] > 0) {
+                CK(cudaMemcpyAsync(A + o_off[i], host_offsets[i], 4 * (size_t)(n_splines[i] + 1),
+                                   cudaMemcpyHostToDevice, st));
+                CK(cudaMemcpyAsync(A + o_pts[i], host_pts[i], 8 * (size_t)n_points[i], cudaMemcpyHostToDevice, st));
+            }
+            gf_spline_frame g;
+            g.H = H[i]; g.W = W[i];
+            g.labels = (const uint8_t *)(A + o_lab[i]);
+            g.n_splines = n_splines[i];
+            g.n_points = n_points[i];
+            g.offsets = (const int32_t *)(A + o_off[i]);
+            g.pts = (const float *)(A + o_pts[i]);
+            g.guide = (float *)(A + o_g[i]);
+            sf.push_back(g);
+        }
+        gf_frame &f = fr[i];
+        f.H = H[i]; f.W = W[i];
+        f.rgba = (const float *)(A + o_rgba[i]);
+        f.labels = (const uint8_t *)(A + o_lab[i]);
+        f.guide = (const float *)(A + o_g[i]);
+        f.out_rgba = (float *)(A + o_rgba[i]);
+        f.out_shell = (int32_t *)(A + o_sh[i]);
+        f.out_enter = nullptr;
+        f.out_stall = nullptr;
+    }
+    if (!sf.empty()) {
+        s = gf_guidance_batched(ctx, (int)sf.size(), sf.data(), eta, stream);
+        if (s != GF_OK) return s;
+    }
+    s = enqueue_fill(ctx, n, fr.data(), params, (gf_stats *)(A + o_st), st);
+    if (s != GF_OK) return s;
+    for (int i = 0; i < n; i++) {
+        size_t np = (size_t)H[i] * W[i];
+        CK(cudaMemcpyAsync(host_out_rgba[i], A + o_rgba[i], 16 * np, cudaMemcpyDeviceToHost, st));
+        CK(cudaMemcpyAsync(host_out_shell[i], A + o_sh[i], 4 * np, cudaMemcpyDeviceToHost, st));
+    }
+    CK(cudaMemcpyAsync(host_stats, A + o_st, sizeof(gf_stats) * (size_t)n, cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    return GF_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,832 @@
+// Shell-by-shell transport fill (Guidefill, arxiv 1611.05319) for sm_103a.
+//
+// Kernels:
+//   init_kernel   one pass over every frame: state word per pixel (out_shell),
+//                 per 8x8 tile the bitmask of hole pixels (U) and of the initial
+//                 active boundary (Qw = d_active D^(0)_h, Notation) built with
+//                 warp ballots, per-frame hole count.
+//   order_kernel  sorts frames by hole size (largest first) into the work queue.
+//   fill_kernel   persistent; one thread-block cluster runs one frame's whole
+//                 shell loop (Algorithm 1) at a time, with one hardware cluster
+//                 barrier per step, then takes the next frame from the queue.
+//
+// Front tracking.  Per step k the cluster processes a work list of tiles.  A
+// tile is on the list of step k+1 iff a pixel was filled at step k within
+// reach (ceil(eps)+1 pixels) of it; the tiles are claimed with atomicMax on a
+// per-tile step word and appended with warp-aggregated atomics (a warp-ballot
+// stream compaction).  Inside a tile only pixels within reach of a step-k fill
+// are candidates: the only pixels whose ready test can change (new front
+// pixels are 8-neighbours of fills, and a waiting pixel's test depends only on
+// pixels of its ball).  Candidates get the exact active-boundary test from the
+// state words, so the front sets equal a full rescan (Algorithm 1, last line).
+// With GF_FLAG_RESCAN every step instead re-tests every unfilled pixel of the
+// frame ("Guidefill without tracking", Section 3.6).
+//
+// State word s per pixel: -1 known, -2 unfilled hole, -3 bystander, k filled at
+// step k.  Readable at step k (Omega_h \ (D^(k)_h u B_h), Section 2.1) iff
+// (uint)(s+1) < (uint)(k+1).  Step-k fills write k, which no step-k test
+// treats as readable, so fills are written in place (Algorithm 1 evaluates
+// every front pixel against D^(k)).
+//
+// Mutable global data is read with ld.global.cg (L2) so that no SM reads a
+// stale L1 line written by another SM of the cluster.
+
+#include <cooperative_groups.h>
+
+#include "gf_internal.cuh"
+
+namespace cg = cooperative_groups;
+
+namespace gf {
+
+constexpr unsigned FULL = 0xffffffffu;
+
+// ---------------------------------------------------------------------------
+// init
+// ---------------------------------------------------------------------------
+// CTA = 256 threads = one strip of 8 rows x 256 columns (32 tiles) of a frame.
+
+__global__ void __launch_bounds__(256) init_kernel(const __grid_constant__ InitArgs a)
+{
+    __shared__ uint8_t lab_s[10][264];
+    int b = blockIdx.x;
+    int lo = 0, hi = a.n_frames;  // frame f with cta_offset[f] <= b < cta_offset[f+1]
+    while (hi - lo > 1) {
+        int mid = (lo + hi) >> 1;
+        if (__ldg(&a.cta_offset[mid]) <= b) lo = mid; else hi = mid;
+    }
+    const FrameDev &F = a.frames[lo];
+    const int H = F.H, W = F.W;
+    const int strips = (W + 255) >> 8;
+    const int local = b - __ldg(&a.cta_offset[lo]);
+    const int ty = local / strips;
+    const int x0 = (local - ty * strips) * 256;
+    const int y0 = ty * TILE;
+    const int t = threadIdx.x;
+
+    // labels of rows y0-1 .. y0+8, columns x0-1 .. x0+256 (0xff outside the image)
+    for (int e = t; e < 10 * 258; e += 256) {
+        int r = e / 258, c = e - r * 258;
+        int y = y0 - 1 + r, x = x0 - 1 + c;
+        uint8_t v = 0xff;
+        if (y >= 0 && y < H && x >= 0 && x < W) v = __ldg(&F.labels[(size_t)y * W + x]);
+        lab_s[r][c] = v;
+    }
+    __syncthreads();
+
+    const int x = x0 + t;
+    const int lane = t & 31;
+    unsigned long long Um[4] = {0, 0, 0, 0}, Qm[4] = {0, 0, 0, 0};
+#pragma unroll
+    for (int r = 0; r < TILE; r++) {
+        int y = y0 + r;
+        bool in = (y < H) && (x < W);
+        uint8_t l = in ? lab_s[r + 1][t + 1] : 0xff;
+        bool hole = in && l == 1;
+        bool front = false;
+        if (hole) {
+#pragma unroll
+            for (int dy = 0; dy < 3; dy++)
+#pragma unroll
+                for (int dx = 0; dx < 3; dx++)
+                    if (!(dx == 1 && dy == 1) && lab_s[r + dy][t + dx] == 0) front = true;
+        }
+        if (in) {
+            int32_t s = (l == 0) ? SH_KNOWN : (l == 1 ? SH_UNFILLED : SH_BYST);
+            F.shell[(size_t)y * W + x] = s;
+            if (F.enter) F.enter[(size_t)y * W + x] = front ? 0 : -1;
+        }
+        unsigned hb = __ballot_sync(FULL, hole);
+        unsigned fb = __ballot_sync(FULL, front);
+#pragma unroll
+        for (int q = 0; q < 4; q++) {
+            Um[q] |= (unsigned long long)((hb >> (8 * q)) & 0xffu) << (8 * r);
+            Qm[q] |= (unsigned long long)((fb >> (8 * q)) & 0xffu) << (8 * r);
+        }
+    }
+    const int warp = t >> 5;
+    if (lane < 4) {
+        int tx = (x0 >> 3) + warp * 4 + lane;
+        if (tx < F.TW && y0 < H) {
+            int tile = ty * F.TW + tx;
+            unsigned long long u = lane == 0 ? Um[0] : lane == 1 ? Um[1] : lane == 2 ? Um[2] : Um[3];
+            unsigned long long q = lane == 0 ? Qm[0] : lane == 1 ? Qm[1] : lane == 2 ? Qm[2] : Qm[3];
+            F.U[tile] = u;
+            F.Qw[tile] = q;
+            F.sched[tile] = -1;
+            F.F[tile].tag = INT32_MIN;
+            F.F[F.ntiles + tile].tag = INT32_MIN;
+            int c = __popcll(u);
+            if (c) atomicAdd(F.holes, c);
+        }
+    }
+}
+
+__global__ void upload_frames_kernel(const __grid_constant__ FrameChunk c)
+{
+    for (int i = threadIdx.x; i < c.count; i += blockDim.x) {
+        c.dst_frames[c.first + i] = c.frames[i];
+        c.dst_cta[c.first + i] = c.cta[i];
+    }
+    if (threadIdx.x == 0 && c.last_chunk) c.dst_cta[c.first + c.count] = c.cta[c.count];
+}
+
+// Frames in decreasing hole size (ties: index), one thread per frame.
+__global__ void order_kernel(const FrameDev *frames, int n, int32_t *order, int32_t *cursor)
+{
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        int hi = __ldcg(frames[i].holes);
+        int rank = 0;
+        for (int j = 0; j < n; j++) {
+            int hj = __ldcg(frames[j].holes);
+            if (hj > hi || (hj == hi && j < i)) rank++;
+        }
+        order[rank] = i;
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) *cursor = 0;
+}
+
+// ---------------------------------------------------------------------------
+// fill
+// ---------------------------------------------------------------------------
+enum Mode { NORMAL = 0, RESCAN = 1, STALL = 2 };
+
+template <int RW>
+struct WarpSmem {
+    static constexpr int WS = TILE + 2 * RW;
+    float4 col[WS * WS];         // colour window (cp.async)
+    uint32_t rowmask[WS];        // readable bits of the window rows
+    float tmin[64];              // per tile pixel: smallest readable weight exponent
+    unsigned long long ready;
+};
+
+__device__ __forceinline__ int nth_bit64(unsigned long long m, int q)
+{
+    int pos = 0;
+#pragma unroll
+    for (int w = 32; w >= 1; w >>= 1) {
+        unsigned long long low = m & ((1ull << w) - 1ull);
+        int c = __popcll(low);
+        if (q >= c) {
+            q -= c;
+            m >>= w;
+            pos += w;
+        } else {
+            m = low;
+        }
+    }
+    return pos;
+}
+
+__device__ __forceinline__ void cp_async16(void *smem, const void *gmem)
+{
+    unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all()
+{
+    asm volatile("cp.async.wait_all;\n" ::: "memory");
+}
+
+// Pixels of the centre tile within Chebyshev distance `reach` of a set bit of
+// the 3x3 neighbourhood masks; lane l < 9 holds the mask of neighbour
+// (dx, dy) = (l%3 - 1, l/3 - 1).  reach <= 8.
+__device__ __forceinline__ unsigned long long dilate_nbr(unsigned long long fm, int reach)
+{
+    const int lane = threadIdx.x & 31;
+    const int gy = lane - 8;  // row in [-8, 16) of the 3-tile column
+    const int tr = gy < 0 ? 0 : (gy < 8 ? 1 : 2);
+    const int ry = (lane < 24) ? gy - (tr - 1) * 8 : 0;
+    unsigned long long mL = __shfl_sync(FULL, fm, tr * 3 + 0);
+    unsigned long long mC = __shfl_sync(FULL, fm, tr * 3 + 1);
+    unsigned long long mR = __shfl_sync(FULL, fm, tr * 3 + 2);
+    uint32_t row = 0;
+    if (lane < 24)
+        row = (uint32_t)((mL >> (8 * ry)) & 0xffu) | ((uint32_t)((mC >> (8 * ry)) & 0xffu) << 8) |
+              ((uint32_t)((mR >> (8 * ry)) & 0xffu) << 16);
+    uint32_t h = row;
+    for (int d = 1; d <= reach; d++) h |= (row << d) | (row >> d);
+    uint32_t hc = (lane < 24) ? ((h >> 8) & 0xffu) : 0u;
+    uint32_t v = 0;
+    for (int d = -reach; d <= reach; d++) {
+        int src = lane + 8 + d;
+        uint32_t xv = __shfl_sync(FULL, hc, src & 31);
+        if (src >= 0 && src < 24) v |= xv;
+    }
+    unsigned long long out = 0;
+#pragma unroll
+    for (int y = 0; y < 8; y++) out |= (unsigned long long)(__shfl_sync(FULL, v, y) & 0xffu) << (8 * y);
+    return out;
+}
+
+// FP64 confidence in the canonical sample order, the same expressions as the
+// oracle (eqs. weight, confidence); used only inside the FP32 guard band.
+template <int RW>
+__device__ bool ready_fp64(const FillParams &p, const WarpSmem<RW> *ws, int px, int py, float gx, float gy,
+                           float ch, float sh, bool ghost)
+{
+    double a2 = __dadd_rn(__dmul_rn((double)gx, (double)gx), __dmul_rn((double)gy, (double)gy));
+    double S_all = 0.0, S_rd = 0.0;
+    for (int s = 0; s < p.tab.ns; s++) {
+        int n = p.tab.cn[s], m = p.tab.cm[s];
+        float ox, oy;
+        if (ghost) {
+            float fn = (float)n, fm = (float)m;
+            ox = __fsub_rn(__fmul_rn(fn, ch), __fmul_rn(fm, sh));
+            oy = __fadd_rn(__fmul_rn(fn, sh), __fmul_rn(fm, ch));
+            float r = rintf(ox);
+            if (fabsf(__fsub_rn(ox, r)) <= p.tau) ox = r;
+            r = rintf(oy);
+            if (fabsf(__fsub_rn(oy, r)) <= p.tau) oy = r;
+        } else {
+            ox = (float)n;
+            oy = (float)m;
+        }
+        float flx = floorf(ox), fly = floorf(oy);
+        float frx = __fsub_rn(ox, flx), fry = __fsub_rn(oy, fly);
+        int ix = px + RW + (int)flx, iy = py + RW + (int)fly;
+        uint32_t need = frx > 0.0f ? 3u : 1u;
+        bool ok = ((ws->rowmask[iy] >> ix) & need) == need;
+        if (fry > 0.0f) ok = ok && (((ws->rowmask[iy + 1] >> ix) & need) == need);
+        double t;
+        if (ghost) {
+            t = __dmul_rn(__dmul_rn(p.coef64, a2), (double)(m * m));
+        } else {
+            double proj = __dadd_rn(__dmul_rn(-(double)gy, (double)n), __dmul_rn((double)gx, (double)m));
+            t = __dmul_rn(__dmul_rn(p.coef64, proj), proj);
+        }
+        double w = __ddiv_rn(exp(-t), __dsqrt_rn((double)(n * n + m * m)));
+        S_all = __dadd_rn(S_all, w);
+        if (ok) S_rd = __dadd_rn(S_rd, w);
+    }
+    double C = __ddiv_rn(S_rd, S_all);
+    return C > p.c64;
+}
+
+struct WarpCounters {
+    int filled, delta, evals, err;
+};
+
+// Processes one tile at step k (one warp).  Returns nothing; updates counters.
+template <int RW, int MODE>
+__device__ void process_tile(const FillParams &p, const FrameDev &F, WarpSmem<RW> *ws, GroupCtl *ctl,
+                             int32_t *lists, int t, int k, unsigned long long cand_in, WarpCounters &wc)
+{
+    constexpr int WS = WarpSmem<RW>::WS;
+    const int lane = threadIdx.x & 31;
+    const int W = F.W, H = F.H;
+    __syncwarp();  // the previous tile's shared-memory reads are complete
+    const int tx = t % F.TW, ty = t / F.TW;
+    const int x0 = tx * TILE, y0 = ty * TILE;
+    const int R = p.tab.R;
+    const bool ghost = (p.flags & GF_FLAG_GHOST) != 0;
+    const bool smart = (p.flags & GF_FLAG_SMART) != 0;
+
+    const unsigned long long U = __ldcg(&F.U[t]);
+    const unsigned long long Qold = __ldcg(&F.Qw[t]);
+    unsigned long long cand;
+    if (MODE == NORMAL) {
+        if (k > 0) {
+            unsigned long long fm = 0;
+            if (lane < 9) {
+                int nx = tx + lane % 3 - 1, ny = ty + lane / 3 - 1;
+                if (nx >= 0 && ny >= 0 && nx < F.TW && ny < F.TH) {
+                    const TileF *e = &F.F[(size_t)((k - 1) & 1) * F.ntiles + (size_t)ny * F.TW + nx];
+                    int tag = __ldcg(&e->tag);
+                    unsigned long long msk = __ldcg(&e->mask);
+                    if (tag == k - 1) fm = msk;
+                }
+            }
+            cand = U & dilate_nbr(fm, R + 1);
+        } else {
+            cand = U;
+        }
+    } else {
+        cand = cand_in & U;
+    }
+    if (cand == 0) return;
+
+    // ---- stage the window: colours asynchronously, readable bits by ballot
+    const int wx0 = x0 - RW, wy0 = y0 - RW;
+    for (int e = lane; e < WS * WS; e += 32) {
+        int r = e / WS, c = e - r * WS;
+        int gx = wx0 + c, gy = wy0 + r;
+        if (gx >= 0 && gy >= 0 && gx < W && gy < H) cp_async16(&ws->col[e], &F.rgba[(size_t)gy * W + gx]);
+    }
+    {
+        int32_t sv[WS];
+#pragma unroll
+        for (int r = 0; r < WS; r++) {
+            int gx = wx0 + lane, gy = wy0 + r;
+            sv[r] = (lane < WS && gx >= 0 && gy >= 0 && gx < W && gy < H) ? __ldcg(&F.shell[(size_t)gy * W + gx])
+                                                                           : SH_OUTSIDE;
+        }
+#pragma unroll
+        for (int r = 0; r < WS; r++) {
+            unsigned b = __ballot_sync(FULL, readable_at(sv[r], k));
+            if (lane == 0) ws->rowmask[r] = b;
+        }
+    }
+    if (lane == 0) ws->ready = 0ull;
+    __syncwarp();
+
+    // ---- exact active-boundary test of the candidates
+    unsigned long long P;
+    {
+        bool f[2];
+#pragma unroll
+        for (int h = 0; h < 2; h++) {
+            int pix = lane + 32 * h;
+            int px = pix & 7, py = pix >> 3;
+            bool c = (cand >> pix) & 1ull;
+            int wc_ = px + RW - 1, wr = py + RW;
+            uint32_t nb = ((ws->rowmask[wr - 1] >> wc_) & 7u) | ((ws->rowmask[wr] >> wc_) & 5u) |
+                          ((ws->rowmask[wr + 1] >> wc_) & 7u);
+            f[h] = c && nb != 0u;
+        }
+        P = (unsigned long long)__ballot_sync(FULL, f[0]) | ((unsigned long long)__ballot_sync(FULL, f[1]) << 32);
+        if (F.enter) {
+            unsigned long long nf = P & ~Qold;
+#pragma unroll
+            for (int h = 0; h < 2; h++) {
+                int pix = lane + 32 * h;
+                if ((nf >> pix) & 1ull)
+                    F.enter[(size_t)(y0 + (pix >> 3)) * W + x0 + (pix & 7)] = k;
+            }
+        }
+    }
+    const int np = __popcll(P);
+    wc.evals += np;
+
+    // ---- ready test (eqs. weight, confidence, ready), G lanes per pixel
+    if (np) {
+        const int G = np <= 4 ? 8 : (np <= 8 ? 4 : (np <= 16 ? 2 : 1));
+        const int per = 32 / G;
+        const int j = lane & (G - 1), grp = lane / G;
+        for (int base = 0; base < np; base += per) {
+            const int q = base + grp;
+            const bool act = q < np;
+            const int pix = act ? nth_bit64(P, q) : 0;
+            const int px = pix & 7, py = pix >> 3;
+            const int gxp = x0 + px, gyp = y0 + py;
+            float2 g = make_float2(0.f, 0.f);
+            if (act && MODE != STALL) g = __ldg(&F.guide[(size_t)gyp * W + gxp]);
+            float ch = 1.0f, sh = 0.0f, beta = 0.0f;
+            const bool rot = ghost && MODE != STALL;
+            if (MODE != STALL) {
+                float a2 = __fadd_rn(__fmul_rn(g.x, g.x), __fmul_rn(g.y, g.y));
+                if (ghost) {
+                    float a = __fsqrt_rn(a2);
+                    if (a > 0.0f) {
+                        ch = __fdiv_rn(g.x, a);
+                        sh = __fdiv_rn(g.y, a);
+                    }
+                    beta = p.coef32 * a2;
+                }
+            }
+            float S_rd = 0.f, S_all = 0.f, tmin = INFINITY;
+            int cnt = 0;
+            for (int gi = 0; gi <= R; gi++) {
+                const float mm = (float)(gi * gi);
+                const float tg = beta * mm;
+                const float eg = (ghost || MODE == STALL) ? expf(-tg) : 0.f;
+                float accg = 0.f;
+                for (int s = p.tab.m_start[gi] + j; s < p.tab.m_start[gi + 1]; s += G) {
+                    const float nf = p.tab.n_f[s], mf = p.tab.m_f[s];
+                    float ox, oy;
+                    if (rot) {
+                        ox = __fsub_rn(__fmul_rn(nf, ch), __fmul_rn(mf, sh));
+                        oy = __fadd_rn(__fmul_rn(nf, sh), __fmul_rn(mf, ch));
+                        float r0 = rintf(ox);
+                        if (fabsf(__fsub_rn(ox, r0)) <= p.tau) ox = r0;
+                        r0 = rintf(oy);
+                        if (fabsf(__fsub_rn(oy, r0)) <= p.tau) oy = r0;
+                    } else {
+                        ox = nf;
+                        oy = mf;
+                    }
+                    const float flx = floorf(ox), fly = floorf(oy);
+                    const float frx = __fsub_rn(ox, flx), fry = __fsub_rn(oy, fly);
+                    const int ix = px + RW + (int)flx, iy = py + RW + (int)fly;
+                    const uint32_t need = frx > 0.0f ? 3u : 1u;
+                    bool ok = ((ws->rowmask[iy] >> ix) & need) == need;
+                    if (fry > 0.0f) ok = ok && (((ws->rowmask[iy + 1] >> ix) & need) == need);
+                    if (ghost || MODE == STALL) {
+                        if (ok) {
+                            accg += p.tab.invd[s];
+                            cnt++;
+                            tmin = fminf(tmin, tg);
+                        }
+                    } else {
+                        // lattice ball: weight exponent per sample
+                        float proj = -g.y * nf + g.x * mf;
+                        float ts = p.coef32 * proj * proj;
+                        float w = expf(-ts) * p.tab.invd[s];
+                        S_all += w;
+                        if (ok) {
+                            S_rd += w;
+                            cnt++;
+                            tmin = fminf(tmin, ts);
+                        }
+                    }
+                }
+                if (ghost || MODE == STALL) {
+                    S_rd += eg * accg;
+                    S_all += eg * p.tab.Dm[gi] * (j == 0 ? 1.f : 0.f);
+                }
+            }
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                if (o < G) {
+                    S_rd += __shfl_xor_sync(FULL, S_rd, o);
+                    S_all += __shfl_xor_sync(FULL, S_all, o);
+                    cnt += __shfl_xor_sync(FULL, cnt, o);
+                    tmin = fminf(tmin, __shfl_xor_sync(FULL, tmin, o));
+                }
+            }
+            bool ready;
+            if (MODE == STALL || !smart) {
+                ready = cnt > 0;
+            } else {
+                const float d = S_rd - p.c * S_all;
+                const float tol = 1e-3f * p.c * S_all;
+                if (d > tol) ready = true;
+                else if (d < -tol) ready = false;
+                else {
+                    ready = false;
+                    if (act && j == 0) ready = ready_fp64<RW>(p, ws, px, py, g.x, g.y, ch, sh, ghost);
+                    ready = __shfl_sync(FULL, ready, lane & ~(G - 1));
+                }
+            }
+            if (act && j == 0 && ready) {
+                atomicOr(&ws->ready, 1ull << pix);
+                ws->tmin[pix] = tmin;
+            }
+        }
+    }
+    cp_async_wait_all();
+    __syncwarp();
+    const unsigned long long Rm = ws->ready;
+    const int nr = __popcll(Rm);
+
+    // ---- fill the ready pixels: normalised weighted average of bilinear ghost values
+    if (nr) {
+        const int G = nr <= 4 ? 8 : (nr <= 8 ? 4 : (nr <= 16 ? 2 : 1));
+        const int per = 32 / G;
+        const int j = lane & (G - 1), grp = lane / G;
+        for (int base = 0; base < nr; base += per) {
+            const int q = base + grp;
+            const bool act = q < nr;
+            const int pix = act ? nth_bit64(Rm, q) : 0;
+            const int px = pix & 7, py = pix >> 3;
+            const int gxp = x0 + px, gyp = y0 + py;
+            float2 g = make_float2(0.f, 0.f);
+            if (act && MODE != STALL) g = __ldg(&F.guide[(size_t)gyp * W + gxp]);
+            float ch = 1.0f, sh = 0.0f, beta = 0.0f;
+            const bool rot = ghost && MODE != STALL;
+            if (MODE != STALL && ghost) {
+                float a2 = __fadd_rn(__fmul_rn(g.x, g.x), __fmul_rn(g.y, g.y));
+                float a = __fsqrt_rn(a2);
+                if (a > 0.0f) {
+                    ch = __fdiv_rn(g.x, a);
+                    sh = __fdiv_rn(g.y, a);
+                }
+                beta = p.coef32 * a2;
+            }
+            const float tmin = act ? ws->tmin[pix] : 0.f;
+            float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+            float wsum = 0.f;
+            if (act) {
+                for (int gi = 0; gi <= R; gi++) {
+                    const float tg = beta * (float)(gi * gi);
+                    const float eg = expf(-(tg - tmin));
+                    for (int s = p.tab.m_start[gi] + j; s < p.tab.m_start[gi + 1]; s += G) {
+                        const float nf = p.tab.n_f[s], mf = p.tab.m_f[s];
+                        float ox, oy;
+                        if (rot) {
+                            ox = __fsub_rn(__fmul_rn(nf, ch), __fmul_rn(mf, sh));
+                            oy = __fadd_rn(__fmul_rn(nf, sh), __fmul_rn(mf, ch));
+                            float r0 = rintf(ox);
+                            if (fabsf(__fsub_rn(ox, r0)) <= p.tau) ox = r0;
+                            r0 = rintf(oy);
+                            if (fabsf(__fsub_rn(oy, r0)) <= p.tau) oy = r0;
+                        } else {
+                            ox = nf;
+                            oy = mf;
+                        }
+                        const float flx = floorf(ox), fly = floorf(oy);
+                        const float frx = __fsub_rn(ox, flx), fry = __fsub_rn(oy, fly);
+                        const int ix = px + RW + (int)flx, iy = py + RW + (int)fly;
+                        const uint32_t need = frx > 0.0f ? 3u : 1u;
+                        bool ok = ((ws->rowmask[iy] >> ix) & need) == need;
+                        if (fry > 0.0f) ok = ok && (((ws->rowmask[iy + 1] >> ix) & need) == need);
+                        if (!ok) continue;
+                        float w;
+                        if (ghost || MODE == STALL) {
+                            w = eg * p.tab.invd[s];
+                        } else {
+                            float proj = -g.y * nf + g.x * mf;
+                            w = expf(-(p.coef32 * proj * proj - tmin)) * p.tab.invd[s];
+                        }
+                        const float4 *cb = &ws->col[iy * WS + ix];
+                        float4 v = cb[0];
+                        float l00 = (1.f - frx) * (1.f - fry);
+                        float4 val = make_float4(l00 * v.x, l00 * v.y, l00 * v.z, l00 * v.w);
+                        if (frx > 0.f) {
+                            float l = frx * (1.f - fry);
+                            float4 c1 = cb[1];
+                            val.x += l * c1.x; val.y += l * c1.y; val.z += l * c1.z; val.w += l * c1.w;
+                        }
+                        if (fry > 0.f) {
+                            float l = (1.f - frx) * fry;
+                            float4 c2 = cb[WS];
+                            val.x += l * c2.x; val.y += l * c2.y; val.z += l * c2.z; val.w += l * c2.w;
+                            if (frx > 0.f) {
+                                float l3 = frx * fry;
+                                float4 c3 = cb[WS + 1];
+                                val.x += l3 * c3.x; val.y += l3 * c3.y; val.z += l3 * c3.z; val.w += l3 * c3.w;
+                            }
+                        }
+                        acc.x += w * val.x; acc.y += w * val.y; acc.z += w * val.z; acc.w += w * val.w;
+                        wsum += w;
+                    }
+                }
+            }
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                if (o < G) {
+                    acc.x += __shfl_xor_sync(FULL, acc.x, o);
+                    acc.y += __shfl_xor_sync(FULL, acc.y, o);
+                    acc.z += __shfl_xor_sync(FULL, acc.z, o);
+                    acc.w += __shfl_xor_sync(FULL, acc.w, o);
+                    wsum += __shfl_xor_sync(FULL, wsum, o);
+                }
+            }
+            if (act && j == 0) {
+                float inv = 1.0f / wsum;
+                F.rgba[(size_t)gyp * W + gxp] = make_float4(acc.x * inv, acc.y * inv, acc.z * inv, acc.w * inv);
+                F.shell[(size_t)gyp * W + gxp] = k;
+            }
+        }
+    }
+
+    // ---- tile bookkeeping
+    const unsigned long long Qnew = (Qold & ~cand) | (P & ~Rm);
+    if (lane == 0) {
+        if (Rm) {
+            F.U[t] = U & ~Rm;
+            TileF *e = &F.F[(size_t)(k & 1) * F.ntiles + t];
+            e->mask = Rm;
+            e->tag = k;
+        }
+        if (Qnew != Qold) F.Qw[t] = Qnew;
+    }
+    wc.filled += nr;
+    wc.delta += __popcll(Qnew) - __popcll(Qold);
+
+    // ---- schedule neighbour tiles for step k+1 (warp-aggregated append)
+    if (MODE != RESCAN && Rm) {
+        const int reach = R + 1;
+        uint32_t colocc = 0, rowocc = 0;
+#pragma unroll
+        for (int y = 0; y < 8; y++) {
+            uint32_t bt = (uint32_t)((Rm >> (8 * y)) & 0xffu);
+            colocc |= bt;
+            if (bt) rowocc |= 1u << y;
+        }
+        const uint32_t lowm = reach >= 8 ? 0xffu : ((1u << reach) - 1u);
+        const bool nL = (colocc & lowm) != 0, nR = (colocc >> (8 - (reach >= 8 ? 8 : reach))) != 0;
+        const bool nU = (rowocc & lowm) != 0, nD = (rowocc >> (8 - (reach >= 8 ? 8 : reach))) != 0;
+        bool claimed = false;
+        int nt = 0;
+        if (lane < 9) {
+            int dx = lane % 3 - 1, dy = lane / 3 - 1;
+            int nx = tx + dx, ny = ty + dy;
+            bool need = (dx == 0 || (dx < 0 ? nL : nR)) && (dy == 0 || (dy < 0 ? nU : nD));
+            if (need && nx >= 0 && ny >= 0 && nx < F.TW && ny < F.TH) {
+                nt = ny * F.TW + nx;
+                claimed = atomicMax(&F.sched[nt], k + 1) < k + 1;
+            }
+        }
+        unsigned bm = __ballot_sync(FULL, claimed);
+        if (bm) {
+            int basei = 0;
+            if (lane == 0) basei = atomicAdd(&ctl->list_count[(k + 1) % 3], __popc(bm));
+            basei = __shfl_sync(FULL, basei, 0);
+            if (claimed) {
+                int pos = basei + __popc(bm & ((1u << lane) - 1u));
+                if (pos < p.list_cap) lists[(size_t)((k + 1) % 3) * p.list_cap + pos] = nt;
+                else wc.err = 1;
+            }
+        }
+    }
+}
+
+template <int RW>
+__device__ __forceinline__ void flush_counters(GroupCtl *ctl, const WarpCounters &wc, int slot3, int slot2,
+                                               bool stall)
+{
+    const int lane = threadIdx.x & 31;
+    int f = wc.filled, d = wc.delta, e = wc.evals, er = wc.err;
+    // all lanes hold identical values except err (per lane)
+    er = __reduce_or_sync(FULL, er);
+    if (lane == 0) {
+        if (!stall) {
+            if (f) atomicAdd(&ctl->filled[slot3], f);
+            if (d) atomicAdd(&ctl->front_delta[slot3], d);
+            if (e) atomicAdd(&ctl->evals[slot3], e);
+            if (er) atomicOr(&ctl->err[slot3], er);
+        } else {
+            if (f) atomicAdd(&ctl->st_filled[slot2], f);
+            if (d) atomicAdd(&ctl->st_front_delta[slot2], d);
+            if (e) atomicAdd(&ctl->evals[slot3], e);
+            if (er) atomicOr(&ctl->st_err[slot2], er);
+        }
+    }
+}
+
+// Every warp of the cluster visits the frame's tiles (32 at a time); `which`
+// selects the tile mask that makes a tile a member (U: rescan, Qw: stall).
+template <int RW, int MODE>
+__device__ void sweep_tiles(const FillParams &p, const FrameDev &F, WarpSmem<RW> *ws, GroupCtl *ctl,
+                            int32_t *lists, int k, int gw, int nw, WarpCounters &wc)
+{
+    const int lane = threadIdx.x & 31;
+    for (int base = gw * 32; base < F.ntiles; base += nw * 32) {
+        int t = base + lane;
+        unsigned long long m = 0;
+        if (t < F.ntiles) m = (MODE == RESCAN) ? __ldcg(&F.U[t]) : __ldcg(&F.Qw[t]);
+        unsigned bal = __ballot_sync(FULL, m != 0ull);
+        while (bal) {
+            int i = __ffs(bal) - 1;
+            bal &= bal - 1;
+            unsigned long long mi = __shfl_sync(FULL, m, i);
+            process_tile<RW, MODE>(p, F, ws, ctl, lists, base + i, k, mi, wc);
+        }
+    }
+}
+
+template <int RW>
+__global__ void __launch_bounds__(CTA_THREADS, 1) fill_kernel(const __grid_constant__ FillParams p)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ FrameDev s_frame;
+    WarpSmem<RW> *ws = reinterpret_cast<WarpSmem<RW> *>(smem_raw) + (threadIdx.x >> 5);
+    cg::cluster_group cluster = cg::this_cluster();
+    const int crank = (int)cluster.block_rank();
+    const int csize = (int)cluster.num_blocks();
+    const int cid = blockIdx.x / csize;
+    GroupCtl *ctl = p.groups + cid;
+    int32_t *lists = p.lists + (size_t)cid * 3 * p.list_cap;
+    const int lane = threadIdx.x & 31;
+    const int gw = (threadIdx.x >> 5) * csize + crank;  // interleave CTAs
+    const int nw = csize * WARPS_PER_CTA;
+    const bool leader = crank == 0 && threadIdx.x == 0;
+    const bool rescan = (p.flags & GF_FLAG_RESCAN) != 0;
+
+    for (int it = 0;; it++) {
+        cluster.sync();  // everyone is done with the previous frame's counters
+        if (leader) {
+            int f = atomicAdd(p.frame_cursor, 1);
+            ctl->cur_frame[it & 1] = f;
+            for (int i = 0; i < 3; i++) {
+                ctl->list_count[i] = 0;
+                ctl->filled[i] = 0;
+                ctl->front_delta[i] = 0;
+                ctl->evals[i] = 0;
+                ctl->err[i] = 0;
+            }
+            for (int i = 0; i < 2; i++) {
+                ctl->st_filled[i] = 0;
+                ctl->st_front_delta[i] = 0;
+                ctl->st_err[i] = 0;
+            }
+            ctl->init_front = 0;
+        }
+        cluster.sync();
+        const int f = __ldcg(&ctl->cur_frame[it & 1]);
+        if (f >= p.n_frames) break;
+        if (threadIdx.x == 0) s_frame = p.frames[p.frame_order[f]];
+        __syncthreads();
+        const FrameDev &F = s_frame;
+
+        // step-0 work list: tiles holding part of the initial active boundary
+        {
+            int cnt = 0;
+            for (int base = gw * 32; base < F.ntiles; base += nw * 32) {
+                int t = base + lane;
+                unsigned long long q = (t < F.ntiles) ? __ldcg(&F.Qw[t]) : 0ull;
+                cnt += __popcll(q);
+                bool has = q != 0ull;
+                unsigned bm = __ballot_sync(FULL, has);
+                if (bm && !rescan) {
+                    int b0 = 0;
+                    if (lane == 0) b0 = atomicAdd(&ctl->list_count[0], __popc(bm));
+                    b0 = __shfl_sync(FULL, b0, 0);
+                    if (has) lists[b0 + __popc(bm & ((1u << lane) - 1u))] = t;
+                }
+            }
+            cnt = __reduce_add_sync(FULL, cnt);
+            if (lane == 0 && cnt) atomicAdd(&ctl->init_front, cnt);
+        }
+        cluster.sync();
+
+        long long n_front = __ldcg(&ctl->init_front);
+        long long filled_tot = 0, evals_tot = 0, max_front = 0;
+        int stalls = 0, status = GF_OK;
+        int k = 0;
+        const int max_shells = F.max_shells;
+        for (;;) {
+            if (leader) {
+                const int s1 = (k + 1) % 3;
+                ctl->filled[s1] = 0;
+                ctl->front_delta[s1] = 0;
+                ctl->evals[s1] = 0;
+                ctl->err[s1] = 0;
+                ctl->list_count[(k + 2) % 3] = 0;
+                ctl->st_filled[k & 1] = 0;
+                ctl->st_front_delta[k & 1] = 0;
+                ctl->st_err[k & 1] = 0;
+            }
+            WarpCounters wc = {0, 0, 0, 0};
+            if (rescan) {
+                sweep_tiles<RW, RESCAN>(p, F, ws, ctl, lists, k, gw, nw, wc);
+            } else {
+                const int slot = k % 3;
+                const int n = __ldcg(&ctl->list_count[slot]);
+                const int32_t *L = lists + (size_t)slot * p.list_cap;
+                for (int i = gw; i < n; i += nw) {
+                    int t = __ldcg(&L[i]);
+                    process_tile<RW, NORMAL>(p, F, ws, ctl, lists, t, k, 0ull, wc);
+                }
+            }
+            flush_counters<RW>(ctl, wc, k % 3, k & 1, false);
+            cluster.sync();
+            const int filled = __ldcg(&ctl->filled[k % 3]);
+            n_front += __ldcg(&ctl->front_delta[k % 3]);
+            evals_tot += __ldcg(&ctl->evals[k % 3]);
+            if (__ldcg(&ctl->err[k % 3])) {
+                status = GF_ERR_INTERNAL;
+                break;
+            }
+            long long front_k = n_front + filled;
+            if (front_k > max_front) max_front = front_k;
+            int fk = filled;
+            if (filled == 0) {
+                if (n_front == 0) break;  // Algorithm 1: D^(k) exhausted (or the rest unreachable)
+                // stall rule: no front pixel is ready; fill the front isotropically
+                WarpCounters ws2 = {0, 0, 0, 0};
+                sweep_tiles<RW, STALL>(p, F, ws, ctl, lists, k, gw, nw, ws2);
+                flush_counters<RW>(ctl, ws2, k % 3, k & 1, true);
+                cluster.sync();
+                const int sf = __ldcg(&ctl->st_filled[k & 1]);
+                n_front += __ldcg(&ctl->st_front_delta[k & 1]);
+                if (__ldcg(&ctl->st_err[k & 1])) {
+                    status = GF_ERR_INTERNAL;
+                    break;
+                }
+                if (sf == 0) break;  // front pixels with no readable sample at all
+                stalls++;
+                fk = sf;
+                if (leader && F.stall_bits) atomicOr(&F.stall_bits[k >> 5], 1u << (k & 31));
+            }
+            filled_tot += fk;
+            k++;
+            if (k >= max_shells) {
+                status = GF_ERR_NO_PROGRESS;
+                break;
+            }
+        }
+        if (leader) {
+            const int holes = __ldcg(F.holes);
+            gf_stats st;
+            st.shells = k;
+            st.stalls = stalls;
+            st.filled = filled_tot;
+            st.evaluations = evals_tot;
+            st.max_front = max_front;
+            st.holes = holes;
+            st.reserved = 0;
+            if (status == GF_OK && filled_tot < holes) status = GF_INCOMPLETE;
+            st.status = status;
+            *F.stats = st;
+        }
+        __syncthreads();
+    }
+}
+
+const void *fill_kernel_entry(int rw)
+{
+    if (rw == 4) return (const void *)fill_kernel<4>;
+    if (rw == 5) return (const void *)fill_kernel<5>;
+    return (const void *)fill_kernel<8>;
+}
+
+cudaError_t launch_fill(int rw, const cudaLaunchConfig_t &cfg, const FillParams &p)
+{
+    if (rw == 4) return cudaLaunchKernelEx(&cfg, fill_kernel<4>, p);
+    if (rw == 5) return cudaLaunchKernelEx(&cfg, fill_kernel<5>, p);
+    return cudaLaunchKernelEx(&cfg, fill_kernel<8>, p);
+}
+
+}  // namespace gf

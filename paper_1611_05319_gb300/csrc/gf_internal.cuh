@@ -1,0 +1,159 @@
+// Internal device-side structures of the Guidefill library (not part of the ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/guidefill.h"
+
+namespace gf {
+
+constexpr int TILE = 8;              // 8x8 pixel tiles; one 64-bit mask per tile
+constexpr int MAX_SAMPLES = 224;     // lattice points with n^2+m^2 <= 64, minus the origin
+constexpr int MAX_R = 8;             // ceil(eps) <= 8
+constexpr int WARPS_PER_CTA = 16;
+constexpr int CTA_THREADS = WARPS_PER_CTA * 32;
+
+// Per-pixel state word (out_shell): readable at step k  <=>  (uint)(s+1) < (uint)(k+1)
+constexpr int32_t SH_KNOWN = -1;
+constexpr int32_t SH_UNFILLED = -2;
+constexpr int32_t SH_BYST = -3;
+constexpr int32_t SH_OUTSIDE = -4;   // only inside staged windows
+
+__host__ __device__ inline bool readable_at(int32_t s, int32_t k) {
+    return (uint32_t)(s + 1) < (uint32_t)(k + 1);
+}
+
+// Sample table of the eps-ball (origin excluded).  The fast path walks the
+// samples grouped by |m| (the weight of a rotated sample depends on m only);
+// the FP64 re-check walks them in canonical order (m ascending, n ascending).
+struct SampleTab {
+    int ns;                      // number of samples
+    int R;                       // ceil(eps)
+    int m_start[MAX_R + 2];      // group |m| = g occupies [m_start[g], m_start[g+1])
+    float Dm[MAX_R + 1];         // sum of 1/|(n,m)| over group g
+    float n_f[MAX_SAMPLES];      // grouped order
+    float m_f[MAX_SAMPLES];
+    float invd[MAX_SAMPLES];     // 1 / sqrt(n^2 + m^2)
+    int8_t cn[MAX_SAMPLES];      // canonical order
+    int8_t cm[MAX_SAMPLES];
+};
+
+struct TileF {                    // fills of one tile at one step
+    unsigned long long mask;
+    int32_t tag;                  // step index the mask belongs to
+    int32_t pad;
+};
+
+// One frame as seen by the kernels.
+struct FrameDev {
+    int32_t H, W, TW, TH, ntiles;
+    int32_t max_shells;
+    float4 *rgba;                 // working image (out_rgba)
+    const uint8_t *labels;
+    const float2 *guide;
+    int32_t *shell;
+    int32_t *enter;               // optional
+    uint32_t *stall_bits;         // optional
+    gf_stats *stats;
+    // scratch (library-owned)
+    unsigned long long *U;        // unfilled hole pixels per tile
+    unsigned long long *Qw;       // front pixels (active boundary, unfilled) per tile
+    TileF *F;                     // [2][ntiles]
+    int32_t *sched;               // last step the tile was scheduled for
+    int32_t *holes;               // |D_h| (written by the init kernel)
+};
+
+// Per-cluster control block (global memory).  Counters are indexed by the step
+// that writes them (mod 3) so that no counter is reset while another CTA of the
+// cluster may still read it.
+struct GroupCtl {
+    int32_t list_count[3];        // work list consumed by step s lives in slot s%3
+    int32_t filled[3];            // fills of step s (normal evaluation)
+    int32_t front_delta[3];       // net change of the front size during step s
+    int32_t evals[3];
+    int32_t err[3];
+    int32_t st_filled[2];         // stall-rule fills of step s (slot s%2)
+    int32_t st_front_delta[2];
+    int32_t st_err[2];
+    int32_t init_front;           // |front_0|
+    int32_t cur_frame[2];
+    int32_t pad[3];
+};
+
+struct FillParams {
+    float eps, mu, c, tau;
+    float coef32;                 // mu^2 / (2 eps^2), FP32
+    double coef64;                // mu^2 / (2 eps^2), FP64 (same expression as the host)
+    double c64;
+    uint32_t flags;
+    int32_t n_frames;
+    int32_t list_cap;             // capacity of each work list (max ntiles)
+    FrameDev *frames;
+    int32_t *frame_order;         // frames in processing order (device)
+    int32_t *frame_cursor;        // device work queue head
+    GroupCtl *groups;             // one per cluster
+    int32_t *lists;               // [n_clusters][3][list_cap]
+    SampleTab tab;
+};
+
+// init kernel arguments: CTA b belongs to frame f with cta_offset[f] <= b < cta_offset[f+1]
+struct InitArgs {
+    const FrameDev *frames;
+    const int32_t *cta_offset;
+    int32_t n_frames;
+};
+
+// guide-field sampler
+constexpr int BIN = 32;       // bins of 32x32 pixels
+constexpr int BIN_CAP = 64;   // segments listed per bin before falling back to a full scan
+
+struct SplineFrameDev {
+    int32_t H, W, NBX, NBY;
+    int32_t n_splines, n_points;
+    const uint8_t *labels;
+    const int32_t *offsets;
+    const float2 *pts;
+    float2 *guide;
+    int32_t *bin_count;  // [NBX*NBY]
+    int32_t *bin_list;   // [NBX*NBY*BIN_CAP]
+};
+
+struct GuideArgs {
+    const SplineFrameDev *frames;
+    const int32_t *point_offset;  // [n+1] first global point of each frame
+    const int32_t *bin_offset;    // [n+1] first global bin of each frame
+    int32_t n_frames;
+    float eta;
+};
+
+// Descriptor upload by value through kernel parameters: no host staging buffer
+// whose lifetime would have to outlast an asynchronous copy or a graph replay.
+constexpr int DESC_CHUNK = 128;
+struct FrameChunk {
+    FrameDev *dst_frames;
+    int32_t *dst_cta;
+    int32_t first, count, last_chunk, pad;
+    FrameDev frames[DESC_CHUNK];
+    int32_t cta[DESC_CHUNK + 1];
+};
+struct SplineChunk {
+    SplineFrameDev *dst_frames;
+    int32_t *dst_po, *dst_bo;
+    int32_t first, count, last_chunk, pad;
+    SplineFrameDev frames[DESC_CHUNK];
+    int32_t po[DESC_CHUNK + 1];
+    int32_t bo[DESC_CHUNK + 1];
+};
+__global__ void upload_frames_kernel(const __grid_constant__ FrameChunk c);
+__global__ void upload_splines_kernel(const __grid_constant__ SplineChunk c);
+
+// Host-side entry points of the templated fill kernel (defined beside it).
+const void *fill_kernel_entry(int rw);
+cudaError_t launch_fill(int rw, const cudaLaunchConfig_t &cfg, const FillParams &p);
+__global__ void init_kernel(const __grid_constant__ InitArgs a);
+__global__ void order_kernel(const FrameDev *frames, int n, int32_t *order, int32_t *cursor);
+__global__ void bin_kernel(const __grid_constant__ GuideArgs a, int total_points);
+__global__ void guide_kernel(const __grid_constant__ GuideArgs a);
+
+}  // namespace gf

@@ -1,0 +1,71 @@
+"""The C ABI library loads and exports every function include/guidefill.h declares (no GPU)."""
+import ctypes as C
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "guidefill.h")
+
+
+def _declared():
+    src = open(HEADER).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    names = re.findall(r"\b(gf_[a-z_0-9]+)\s*\(", src)
+    return sorted(set(names))
+
+
+@pytest.fixture(scope="module")
+def built_lib():
+    from paper_1611_05319_gb300 import build
+    return build.build()
+
+
+def test_header_declares_the_api():
+    names = _declared()
+    for n in ["gf_create", "gf_destroy", "gf_fill", "gf_fill_batched", "gf_guidance_from_splines",
+              "gf_status_string"]:
+        assert n in names
+
+
+def test_library_exports_every_declared_symbol(built_lib):
+    lib = C.CDLL(built_lib)
+    missing = [n for n in _declared() if not hasattr(lib, n)]
+    assert not missing, missing
+    from paper_1611_05319_gb300 import _lib
+    assert sorted(_lib.EXPORTS) == _declared()
+
+
+def test_status_strings_and_argument_errors_without_gpu(built_lib):
+    lib = C.CDLL(built_lib)
+    lib.gf_status_string.restype = C.c_char_p
+    assert lib.gf_status_string(0) == b"ok"
+    assert b"invalid" in lib.gf_status_string(-1)
+    lib.gf_create.argtypes = [C.POINTER(C.c_void_p), C.c_int]
+    lib.gf_create.restype = C.c_int
+    # a NULL output pointer is an argument error detected before any CUDA call
+    assert lib.gf_create(None, 0) == -1
+    # calls on a NULL context are argument errors, nothing is launched
+    lib.gf_fill.restype = C.c_int
+    assert lib.gf_fill(None, None, None, None, None) == -1
+    lib.gf_fill_batched.restype = C.c_int
+    assert lib.gf_fill_batched(None, 1, None, None, None, None) == -1
+    lib.gf_guidance_batched.restype = C.c_int
+    assert lib.gf_guidance_batched(None, 1, None, C.c_float(3.0), None) == -1
+
+
+def test_struct_layouts_match_header(tmp_path):
+    """ctypes mirrors of the ABI structs have the sizes the C compiler gives the header's."""
+    import shutil
+    import subprocess
+    if not shutil.which("gcc"):
+        pytest.skip("gcc not available")
+    src = tmp_path / "sz.c"
+    src.write_text('#include <stdio.h>\n#include "%s"\nint main(void){printf("%%zu %%zu %%zu %%zu",'
+                   'sizeof(gf_frame),sizeof(gf_params),sizeof(gf_spline_frame),sizeof(gf_stats));return 0;}' % HEADER)
+    exe = tmp_path / "sz"
+    subprocess.run(["gcc", str(src), "-o", str(exe)], check=True)
+    sizes = [int(v) for v in subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split()]
+    from paper_1611_05319_gb300 import _lib
+    assert sizes == [C.sizeof(_lib.Frame), C.sizeof(_lib.Params), C.sizeof(_lib.SplineFrame), _lib.STATS_BYTES]

@@ -1,0 +1,292 @@
+"""CUDA path vs the CPU oracle on the same seeded inputs (needs a GB300).
+
+Bar: shell indices and front-entry steps bit-exact, per-frame counts equal,
+colours within 1e-4 max-abs of the FP64 oracle.  Inputs at hole and bystander
+pixels are NaN: the fill must never read them.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from synth import configs
+
+from _gpu import assert_parity, gpu_fill, hole_blobs, oracle_fill, rgba
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _ctx(cuda_device):
+    import paper_1611_05319_gb300 as gf
+    from paper_1611_05319_gb300 import build
+    build.build()
+    return gf.context(0)
+
+
+def _case(H, W, seed, byst=0.03, zero_g=0.2, n=None, rmax=7):
+    rng = np.random.default_rng(seed)
+    n = n if n is not None else max(1, H * W // 300)
+    hole = hole_blobs(H, W, seed, n=n, rmax=rmax, margin=3)
+    b = (rng.uniform(0, 1, (H, W)) < byst) & ~hole
+    lab = synth.labels_from(hole, b)
+    img = rng.uniform(0, 1, (H, W, 3)).astype(np.float32)
+    img[lab != 0] = np.nan
+    g = synth.random_guide(H, W, seed + 1, zero_fraction=zero_g)
+    return img, lab, g
+
+
+def test_plain_128_annulus():
+    d = configs.plain_128(poison=True)
+    o = oracle_fill(d["rgb"], d["labels"], d["guide"], eps=3.0, mu=50.0, c=0.05)
+    g = gpu_fill(d["rgb"], d["labels"], d["guide"], eps=3.0, mu=50.0, c=0.05)
+    assert_parity(o, g, d["labels"])
+    assert g["stats"]["status"] == 0
+
+
+@pytest.mark.parametrize("H,W", [(37, 53), (64, 64), (8, 8), (5, 200), (200, 5), (129, 131), (1, 1), (2, 9)])
+@pytest.mark.parametrize("eps", [3.0, 4.0])
+def test_random_frames_ragged(H, W, eps):
+    img, lab, g = _case(H, W, 1000 + H * 7 + W)
+    o = oracle_fill(img, lab, g, eps=eps, mu=50.0)
+    r = gpu_fill(img, lab, g, eps=eps, mu=50.0)
+    assert_parity(o, r, lab)
+
+
+@pytest.mark.parametrize("eps", [1.0, 1.5, 2.5, 3.3, 5.0, 6.5, 7.0])
+@pytest.mark.parametrize("mu", [0.0, 10.0, 50.0])
+def test_eps_mu_grid(eps, mu):
+    img, lab, g = _case(48, 56, int(eps * 100 + mu))
+    o = oracle_fill(img, lab, g, eps=eps, mu=mu)
+    r = gpu_fill(img, lab, g, eps=eps, mu=mu)
+    assert_parity(o, r, lab)
+
+
+@pytest.mark.parametrize("ghost", [True, False])
+@pytest.mark.parametrize("smart", [True, False])
+@pytest.mark.parametrize("rescan", [False, True])
+def test_flags(ghost, smart, rescan):
+    img, lab, g = _case(60, 72, 77 + ghost + 2 * smart)
+    o = oracle_fill(img, lab, g, eps=3.0, mu=10.0, ghost=ghost, smart=smart)
+    r = gpu_fill(img, lab, g, eps=3.0, mu=10.0, ghost=ghost, smart=smart, rescan=rescan)
+    assert_parity(o, r, lab)
+
+
+def test_rescan_equals_tracking_and_counts_every_front_pixel():
+    d = configs.plain_128(poison=True)
+    a = gpu_fill(d["rgb"], d["labels"], d["guide"], rescan=False)
+    b = gpu_fill(d["rgb"], d["labels"], d["guide"], rescan=True)
+    o = oracle_fill(d["rgb"], d["labels"], d["guide"])
+    assert np.array_equal(a["shell"], b["shell"]) and np.array_equal(a["enter"], b["enter"])
+    assert np.array_equal(a["u"], b["u"])  # same FP32 operations in the same order
+    assert b["stats"]["evaluations"] == o["stats"]["evaluations"]  # rescan evaluates the whole front every step
+    assert a["stats"]["evaluations"] < b["stats"]["evaluations"]
+
+
+@pytest.mark.parametrize("c", [1e-6, 0.05, 0.3, 0.9])
+def test_confidence_thresholds(c):
+    img, lab, g = _case(50, 50, 5)
+    o = oracle_fill(img, lab, g, eps=3.0, mu=5.0, c=c)
+    r = gpu_fill(img, lab, g, eps=3.0, mu=5.0, c=c)
+    assert_parity(o, r, lab)
+
+
+def test_stall_rule_band_across_image():
+    H, W = 24, 40
+    hole = np.zeros((H, W), bool)
+    hole[8:16, :] = True
+    lab = synth.labels_from(hole)
+    g = synth.const_guide(H, W, 0.0)
+    img = np.random.default_rng(9).uniform(0, 1, (H, W, 3)).astype(np.float32)
+    img[hole] = np.nan
+    o = oracle_fill(img, lab, g, mu=50.0)
+    r = gpu_fill(img, lab, g, mu=50.0)
+    assert o["stats"]["stalls"] > 0
+    assert_parity(o, r, lab)
+
+
+def test_walled_region_incomplete():
+    H, W = 30, 30
+    hole = synth.rect_mask(H, W, 5, 5, 8, 8) | synth.rect_mask(H, W, 20, 20, 3, 3)
+    byst = synth.rect_mask(H, W, 19, 19, 5, 5) & ~synth.rect_mask(H, W, 20, 20, 3, 3)
+    lab = synth.labels_from(hole, byst)
+    img = np.random.default_rng(3).uniform(0, 1, (H, W, 3)).astype(np.float32)
+    img[lab == 2] = np.nan
+    g = synth.random_guide(H, W, 4)
+    o = oracle_fill(img, lab, g)
+    r = gpu_fill(img, lab, g)
+    assert_parity(o, r, lab)
+    assert r["stats"]["status"] == 1 and (r["shell"][20:23, 20:23] == -2).all()
+
+
+def test_all_hole_and_no_hole():
+    H, W = 20, 28
+    g = synth.random_guide(H, W, 1)
+    img = np.random.default_rng(2).uniform(0, 1, (H, W, 3)).astype(np.float32)
+    lab = np.ones((H, W), np.uint8)
+    r = gpu_fill(img, lab, g)
+    assert r["stats"]["filled"] == 0 and r["stats"]["status"] == 1 and (r["shell"] == -2).all()
+    lab0 = np.zeros((H, W), np.uint8)
+    r0 = gpu_fill(img, lab0, g)
+    assert r0["stats"]["filled"] == 0 and r0["stats"]["status"] == 0 and (r0["shell"] == -1).all()
+    assert np.array_equal(r0["u"][..., :3], img)
+
+
+def test_hole_touching_every_border():
+    H, W = 33, 47
+    hole = np.zeros((H, W), bool)
+    hole[:4, :] = True
+    hole[-3:, :] = True
+    hole[:, :2] = True
+    hole[:, -5:] = True
+    lab = synth.labels_from(hole)
+    img = np.random.default_rng(4).uniform(0, 1, (H, W, 3)).astype(np.float32)
+    img[hole] = np.nan
+    g = synth.random_guide(H, W, 5)
+    o = oracle_fill(img, lab, g)
+    r = gpu_fill(img, lab, g)
+    assert_parity(o, r, lab)
+
+
+@pytest.mark.parametrize("cs", [1, 2, 4, 8, 16])
+def test_launch_shape_does_not_change_results(cs):
+    import paper_1611_05319_gb300 as gf
+    ctx = gf.context(0)
+    d = configs.plain_128(poison=True)
+    o = oracle_fill(d["rgb"], d["labels"], d["guide"])
+    if ctx.max_active_clusters(3.0, cs) <= 0:
+        pytest.skip(f"cluster size {cs} not schedulable")
+    ctx.set_launch_config(cluster_size=cs)
+    try:
+        r = gpu_fill(d["rgb"], d["labels"], d["guide"])
+        assert ctx.last_launch()[0] == cs
+    finally:
+        ctx.set_launch_config(0)
+    assert_parity(o, r, d["labels"])
+
+
+def test_batched_mixed_sizes_and_params():
+    import torch
+
+    import paper_1611_05319_gb300 as gf
+    ctx = gf.context(0)
+    cases = [_case(H, W, 300 + i) for i, (H, W) in enumerate([(40, 40), (17, 93), (128, 64), (9, 9), (70, 71)])]
+    res = ctx.fill_batched([torch.from_numpy(rgba(c[0])).cuda() for c in cases],
+                           [torch.from_numpy(c[1]).cuda() for c in cases],
+                           [torch.from_numpy(c[2]).cuda() for c in cases], eps=3.0, mu=20.0, enter=True, stall=True)
+    torch.cuda.synchronize()
+    for (img, lab, g), r in zip(cases, res):
+        gg = dict(u=r.rgba.cpu().numpy(), shell=r.shell.cpu().numpy(), enter=r.enter.cpu().numpy(),
+                  stats=r.stats(), stall_steps=r.stall_steps())
+        o = oracle_fill(img, lab, g, eps=3.0, mu=20.0)
+        assert_parity(o, gg, lab)
+
+
+def test_in_place_and_host_buffers_match():
+    import torch
+
+    import paper_1611_05319_gb300 as gf
+    ctx = gf.context(0)
+    img, lab, g = _case(64, 80, 11)
+    a = gpu_fill(img, lab, g)
+    x = torch.from_numpy(rgba(img)).cuda()
+    r = ctx.fill(x, torch.from_numpy(lab).cuda(), torch.from_numpy(g).cuda(), out="inplace")
+    torch.cuda.synchronize()
+    assert r.rgba.data_ptr() == x.data_ptr()
+    assert np.array_equal(x.cpu().numpy()[a["shell"] >= 0], a["u"][a["shell"] >= 0])
+    out_rgba = np.zeros((64, 80, 4), np.float32)
+    out_shell = np.zeros((64, 80), np.int32)
+    st = ctx.fill_batched_host([rgba(img)], [lab], [g], [out_rgba], [out_shell])
+    assert np.array_equal(out_shell, a["shell"])
+    assert np.array_equal(out_rgba[a["shell"] >= 0], a["u"][a["shell"] >= 0])
+    assert st[0]["filled"] == a["stats"]["filled"]
+
+
+def test_repeated_calls_are_deterministic():
+    d = configs.plain_128(poison=True)
+    a = gpu_fill(d["rgb"], d["labels"], d["guide"])
+    b = gpu_fill(d["rgb"], d["labels"], d["guide"])
+    assert np.array_equal(a["shell"], b["shell"]) and np.array_equal(a["u"], b["u"])
+
+
+# ---------------------------------------------------------------------------
+# guide field from splines
+# ---------------------------------------------------------------------------
+def _gpu_guidance(lab, off, pts, eta):
+    import torch
+
+    import paper_1611_05319_gb300 as gf
+    g = gf.context(0).guidance(torch.from_numpy(lab).cuda(), off, pts, eta)
+    torch.cuda.synchronize()
+    return g.cpu().numpy()
+
+
+def test_guidance_small_bitexact():
+    H, W = 90, 130
+    ctrl = synth.random_beziers(5, H, W, 3, 40.0, margin=5)
+    off, pts = synth.flatten_beziers(ctrl, 16)
+    lab = synth.labels_from(synth.band_mask(H, W, ctrl, [6.0] * 5))
+    go = oracle.guidance(lab, off, pts, 3.0)
+    gg = _gpu_guidance(lab, off, pts, 3.0)
+    hole = lab == 1
+    assert np.array_equal(go[hole], gg[hole])
+
+
+def test_guidance_overflowing_bins_bitexact():
+    """Many short segments through one bin: the bin list overflows and the
+    kernel scans every segment of the frame."""
+    H, W = 64, 64
+    t = np.linspace(0, 2 * np.pi, 200)
+    pts = np.stack([32 + 10 * np.cos(t), 32 + 10 * np.sin(t)], 1).astype(np.float32)
+    off = np.array([0, 200], np.int32)
+    lab = np.ones((H, W), np.uint8)
+    go = oracle.guidance(lab, off, pts, 2.0)
+    gg = _gpu_guidance(lab, off, pts, 2.0)
+    assert np.array_equal(go, gg)
+
+
+# ---------------------------------------------------------------------------
+# full-size workloads (launch configuration of the benchmark)
+# ---------------------------------------------------------------------------
+def test_frame_1080_full_size_sampler_and_fill():
+    d = configs.frame_1080(poison=True)
+    lab = d["labels"]
+    go = oracle.guidance(lab, *d["splines"], eta=3.0)
+    gg = _gpu_guidance(lab, *d["splines"], eta=3.0)
+    assert np.array_equal(go[lab == 1], gg[lab == 1])
+    o = oracle_fill(d["rgb"], lab, go)
+    assert o["stats"]["min_margin"] > 1e-10
+    r = gpu_fill(d["rgb"], lab, go)
+    assert_parity(o, r, lab)
+
+
+@pytest.mark.slow
+def test_frame_4k_blob_full_size():
+    d = configs.frame_4k_blob(poison=True)
+    lab = d["labels"]
+    go = oracle.guidance(lab, *d["splines"], eta=3.0)
+    o = oracle_fill(d["rgb"], lab, go, eps=4.0)
+    for rescan in (False, True):
+        r = gpu_fill(d["rgb"], lab, go, eps=4.0, rescan=rescan)
+        assert_parity(o, r, lab)
+
+
+def test_batch_1080_sampled_frames_in_bench_launch():
+    """Three frames of the 64-frame batch (smallest, a middle one, the largest
+    hole fraction) filled together in one batched launch."""
+    import torch
+
+    import paper_1611_05319_gb300 as gf
+    ctx = gf.context(0)
+    seeds = [100, 131, 163]
+    frames = [configs.batch_frame(s, poison=True) for s in seeds]
+    guides = [oracle.guidance(f["labels"], *f["splines"], eta=3.0) for f in frames]
+    res = ctx.fill_batched([torch.from_numpy(rgba(f["rgb"])).cuda() for f in frames],
+                           [torch.from_numpy(f["labels"]).cuda() for f in frames],
+                           [torch.from_numpy(g).cuda() for g in guides], enter=True, stall=True)
+    torch.cuda.synchronize()
+    for f, g, r in zip(frames, guides, res):
+        gg = dict(u=r.rgba.cpu().numpy(), shell=r.shell.cpu().numpy(), enter=r.enter.cpu().numpy(),
+                  stats=r.stats(), stall_steps=r.stall_steps())
+        o = oracle_fill(f["rgb"], f["labels"], g)
+        assert_parity(o, gg, f["labels"])
