@@ -56,7 +56,8 @@ __global__ void __launch_bounds__(256) bin_kernel(const __grid_constant__ GuideA
         int mid = (lo + hi) >> 1;
         if (__ldg(&F.offsets[mid]) <= i) lo = mid; else hi = mid;
     }
-    if (F.n_splines <= 0 || i < __ldg(&F.offsets[0]) || i + 1 >= __ldg(&F.offsets[lo + 1])) return;
+    if (F.n_splines <= 0 || i + 1 >= F.n_points || i < __ldg(&F.offsets[0]) || i + 1 >= __ldg(&F.offsets[lo + 1]))
+        return;
     float2 A = __ldg(&F.pts[i]), B = __ldg(&F.pts[i + 1]);
     float vx = __fsub_rn(B.x, A.x), vy = __fsub_rn(B.y, A.y);
     float l2 = __fadd_rn(__fmul_rn(vx, vx), __fmul_rn(vy, vy));
@@ -130,7 +131,7 @@ __global__ void __launch_bounds__(256) guide_kernel(const __grid_constant__ Guid
             }
         } else {
             for (int sp = 0; sp < F.n_splines; sp++) {
-                int i0 = __ldg(&F.offsets[sp]), i1 = __ldg(&F.offsets[sp + 1]);
+                int i0 = max(0, __ldg(&F.offsets[sp])), i1 = min(F.n_points, __ldg(&F.offsets[sp + 1]));
                 for (int i = i0; i + 1 < i1; i++) {
                     float2 A = __ldg(&F.pts[i]), B = __ldg(&F.pts[i + 1]);
                     float vx = __fsub_rn(B.x, A.x), vy = __fsub_rn(B.y, A.y);
