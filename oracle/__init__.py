@@ -71,10 +71,10 @@ def lib():
         if hasattr(_lib, "oracle_frozen_fill"):
             _lib.oracle_frozen_fill.restype = C.c_int
             _lib.oracle_frozen_fill.argtypes = [C.c_int, C.c_int, C.c_int, P, P, P, P, C.c_double,
-                                                C.c_double, C.c_float, P, P, P, C.c_int, P]
+                                                C.c_double, C.c_float, P, P, C.c_int, P]
             _lib.oracle_fill_backward.restype = C.c_int
-            _lib.oracle_fill_backward.argtypes = [C.c_int, C.c_int, C.c_int, P, P, P, P, C.c_double,
-                                                  C.c_double, C.c_float, P, P, C.c_int, P, P, P, P]
+            _lib.oracle_fill_backward.argtypes = [C.c_int, C.c_int, C.c_int, P, P, P, C.c_double, C.c_double,
+                                                  C.c_float, P, P, C.c_int, P, P, P, P]
     return _lib
 
 
@@ -135,3 +135,50 @@ def alg_bytes(labels, guide, eps, shell, enter, ghost=True, tau=1e-5):
     return int(lib().oracle_alg_bytes(H, W, _p(lab), _p(g), _f32(eps), GHOST if ghost else 0,
                                       _f32(tau), _p(np.ascontiguousarray(shell, np.int32)),
                                       _p(np.ascontiguousarray(enter, np.int32))))
+
+
+# ---------------------------------------------------------------------------
+# adjoint (frozen schedule): see guidefill_oracle_adjoint.c
+# ---------------------------------------------------------------------------
+def _stall_u8(stall_steps, K):
+    s = np.zeros(max(K, 1), np.uint8)
+    if stall_steps is not None and len(stall_steps):
+        s[:len(stall_steps)] = np.asarray(stall_steps, np.uint8)[:K]
+    return s
+
+
+def frozen_fill(u_in, labels, guide, shell, stall_steps, eps=3.0, mu=50.0, phi=None, tau=1e-5):
+    """FP64 fill with the schedule (shell map, stall steps) and the ghost-sample
+    taps of a forward run held fixed, at angle field ``phi`` (FP64 [H, W]; None =
+    angle of ``guide``) and ``mu``.  Returns u_out FP64 [H, W, C]."""
+    lab = np.ascontiguousarray(labels, np.uint8)
+    H, W = lab.shape
+    u = np.ascontiguousarray(u_in, np.float64)
+    Cn = u.shape[2]
+    out = np.empty_like(u)
+    g = np.ascontiguousarray(guide, np.float32)
+    sh = np.ascontiguousarray(shell, np.int32)
+    K = int(sh.max()) + 1 if sh.size else 0
+    ph = None if phi is None else np.ascontiguousarray(phi, np.float64)
+    lib().oracle_frozen_fill(H, W, Cn, _p(u), _p(lab), _p(g), _p(ph), _f32(eps), float(mu), _f32(tau), _p(sh),
+                             _p(_stall_u8(stall_steps, K)), K, _p(out))
+    return out
+
+
+def fill_backward(u_out, labels, guide, shell, stall_steps, grad_out, eps=3.0, mu=50.0, tau=1e-5):
+    """FP64 reverse sweep of the frozen fill.  Returns (grad_in [H,W,C],
+    grad_phi [H,W], grad_mu)."""
+    lab = np.ascontiguousarray(labels, np.uint8)
+    H, W = lab.shape
+    u = np.ascontiguousarray(u_out, np.float64)
+    Cn = u.shape[2]
+    go = np.ascontiguousarray(grad_out, np.float64)
+    gi = np.empty_like(go)
+    gphi = np.empty((H, W), np.float64)
+    gmu = C.c_double(0.0)
+    sh = np.ascontiguousarray(shell, np.int32)
+    K = int(sh.max()) + 1 if sh.size else 0
+    g = np.ascontiguousarray(guide, np.float32)
+    lib().oracle_fill_backward(H, W, Cn, _p(u), _p(lab), _p(g), _f32(eps), float(mu), _f32(tau), _p(sh),
+                               _p(_stall_u8(stall_steps, K)), K, _p(go), _p(gi), _p(gphi), C.byref(gmu))
+    return gi, gphi, gmu.value
