@@ -198,6 +198,47 @@ gf_status gf_guidance_batched(gf_ctx *ctx, int n, const gf_spline_frame *frames,
                               void *stream);
 
 /*
+ * Guide field from an angle field: g = mag * (cos phi, sin phi) at hole pixels
+ * (labels == 1), evaluated in FP64 and rounded once to FP32; other pixels are
+ * not written.  mag, phi: [H][W] float (phi in radians, x towards columns,
+ * y towards rows).  The parametrisation in which gf_fill_backward reports the
+ * angle gradient.
+ */
+gf_status gf_guide_from_angle(gf_ctx *ctx, int H, int W, const uint8_t *labels, const float *mag,
+                              const float *phi, float *guide, void *stream);
+
+/* One frame of an adjoint request (all DEVICE pointers). */
+typedef struct {
+    int32_t H, W;
+    const float *out_rgba;   /* [H][W][4] the forward's output */
+    const float *guide;      /* [H][W][2] the forward's guide field */
+    const int32_t *shell;    /* [H][W] the forward's shell map */
+    const uint32_t *stall;   /* the forward's stall bitmap, or NULL if it had none */
+    const float *grad_out;   /* [H][W][4] dL / d out_rgba */
+    float *grad_in;          /* [H][W][4] dL / d rgba (may equal grad_out) */
+    float *grad_phi;         /* [H][W] dL / d(angle of g) at fixed |g|; 0 where g = 0,
+                                at stall-filled and at unfilled pixels */
+    float *grad_mu;          /* one float: this frame's dL / d mu (overwritten) */
+} gf_adjoint_frame;
+
+/*
+ * Adjoint of gf_fill / gf_fill_batched (reverse sweep over the steps of
+ * Algorithm 1, K-1 .. 0), for the rotated ghost-pixel ball (GF_FLAG_GHOST;
+ * otherwise GF_ERR_UNSUPPORTED).  The fill is differentiated as a map of the
+ * known colours, the guidance angle field and mu with the shell schedule, the
+ * stall steps and each sample's set of bilinear taps held fixed (piecewise
+ * constant, derivative zero almost everywhere).  The forward's shell map
+ * reconstructs every D^(k); no other forward state is needed.  params must be
+ * those of the forward call.  grad_in is zero at filled hole pixels (their
+ * input colour is never read) and equals grad_out at every other pixel plus
+ * the contributions of the fills that read it.  Scatters use float atomics,
+ * so the summation order (and the last bits) may vary between runs.
+ * frames: HOST array of n descriptors.
+ */
+gf_status gf_fill_backward(gf_ctx *ctx, int n, const gf_adjoint_frame *frames, const gf_params *params,
+                           void *stream);
+
+/*
  * Launch shape of the persistent fill (no counterpart in the paper; a tuning
  * knob of this implementation).  cluster_size in {0 (automatic), 1, 2, 4, 8,
  * 16} CTAs per frame; n_clusters = number of persistent clusters (0 = as many

@@ -132,9 +132,11 @@ static int pixel_samples(const adjctx *A, int x, int y, double phi, double mu, p
     int iso = A->stall[k] != 0;
     float gx = A->guide[2 * p], gy = A->guide[2 * p + 1];
     double a2 = (double)gx * (double)gx + (double)gy * (double)gy;
-    double a = sqrt(a2);
     double c = cos(phi), s = sin(phi);
-    if (iso || !(sqrtf(gx * gx + gy * gy) > 0.0f)) {
+    float g2 = gx * gx;
+    g2 = g2 + gy * gy;
+    const int dir = !iso && sqrtf(g2) > 0.0f; /* the forward rotates only where the FP32 |g| > 0 */
+    if (!dir) {
         c = 1.0;
         s = 0.0;
     }
@@ -154,8 +156,8 @@ static int pixel_samples(const adjctx *A, int x, int y, double phi, double mu, p
         ce->ok = ok;
         P->px[i] = x + n * c - m * s;
         P->py[i] = y + n * s + m * c;
-        P->dpx[i] = (iso || a == 0.0) ? 0.0 : (-n * s - m * c);
-        P->dpy[i] = (iso || a == 0.0) ? 0.0 : (n * c - m * s);
+        P->dpx[i] = dir ? (-n * s - m * c) : 0.0;
+        P->dpy[i] = dir ? (n * c - m * s) : 0.0;
         t[i] = iso ? 0.0 : mu * mu * a2 * (double)(m * m) * A->coef;
         P->lam[i] = iso ? 0.0 : -2.0 * mu * a2 * (double)(m * m) * A->coef;
         if (ok) {

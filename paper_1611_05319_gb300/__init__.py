@@ -159,6 +159,53 @@ class Context:
         check(lib().gf_fill_batched_ex(self._h, len(frames), frames, C.byref(params), _ptr(stats), _stream(stream),
                                        e0, e1), "gf_fill_batched_ex", self._h)
 
+    # --------------------------------------------------------------- adjoint
+    def fill_backward(self, results: Sequence[FillResult], guides: Sequence[torch.Tensor],
+                      grad_out: Sequence[torch.Tensor], eps=3.0, mu=50.0, c=0.05, smart=True, snap_tau=1e-5,
+                      max_shells=0, stream=None):
+        """Adjoint of ``fill_batched`` (ghost ball): returns lists (grad_in [H,W,4],
+        grad_phi [H,W]) and a device tensor grad_mu [n] (one value per frame).
+        ``results`` must come from a fill with ``stall=True`` when it had stall steps."""
+        n = len(results)
+        dev = torch.device("cuda", self.device)
+        frames = (_lib.AdjointFrame * n)()
+        gi, gp, keep = [], [], []
+        gmu = torch.zeros((n,), dtype=torch.float32, device=dev)
+        for i, r in enumerate(results):
+            H, W = r.shell.shape
+            go = grad_out[i].to(dev, torch.float32).contiguous()
+            if go.shape[-1] == 3:
+                go = torch.cat([go, torch.zeros_like(go[..., :1])], dim=2).contiguous()
+            g = guides[i].to(dev, torch.float32).contiguous()
+            a = torch.empty((H, W, 4), dtype=torch.float32, device=dev)
+            b = torch.empty((H, W), dtype=torch.float32, device=dev)
+            frames[i] = _lib.AdjointFrame(H, W, r.rgba.data_ptr(), g.data_ptr(), r.shell.data_ptr(),
+                                          r.stall.data_ptr() if r.stall is not None else None, go.data_ptr(),
+                                          a.data_ptr(), b.data_ptr(), gmu.data_ptr() + 4 * i)
+            gi.append(a)
+            gp.append(b)
+            keep.append((go, g))
+        prm = make_params(eps, mu, c, True, smart, False, snap_tau, max_shells)
+        with torch.cuda.device(self.device):
+            check(lib().gf_fill_backward(self._h, n, frames, C.byref(prm), _stream(stream)), "gf_fill_backward",
+                  self._h)
+        self._akeep = keep
+        return gi, gp, gmu
+
+    def guide_from_angle(self, labels, mag, phi, out=None, stream=None) -> torch.Tensor:
+        """g = mag (cos phi, sin phi) at hole pixels (FP64, rounded once)."""
+        dev = torch.device("cuda", self.device)
+        lab = labels.to(dev, torch.uint8).contiguous()
+        m = mag.to(dev, torch.float32).contiguous()
+        p = phi.to(dev, torch.float32).contiguous()
+        H, W = lab.shape
+        g = out if out is not None else torch.zeros((H, W, 2), dtype=torch.float32, device=dev)
+        with torch.cuda.device(self.device):
+            check(lib().gf_guide_from_angle(self._h, H, W, _ptr(lab), _ptr(m), _ptr(p), _ptr(g), _stream(stream)),
+                  "gf_guide_from_angle", self._h)
+        self._gakeep = (lab, m, p)
+        return g
+
     # -------------------------------------------------------------- guidance
     def guidance(self, labels, offsets, pts, eta=3.0, out=None, stream=None) -> torch.Tensor:
         """Guide field from polylines (Section 3.3), written at hole pixels of ``out``

@@ -23,7 +23,8 @@ STATUS = {0: "ok", 1: "incomplete", -1: "invalid argument", -2: "CUDA error", -3
 # every function declared in include/guidefill.h
 EXPORTS = ["gf_create", "gf_destroy", "gf_status_string", "gf_last_cuda_error", "gf_fill",
            "gf_fill_batched", "gf_fill_batched_ex", "gf_fill_batched_host", "gf_guidance_from_splines", "gf_guidance_batched",
-           "gf_set_launch_config", "gf_get_last_launch", "gf_max_active_clusters"]
+           "gf_set_launch_config", "gf_get_last_launch", "gf_max_active_clusters", "gf_fill_backward",
+           "gf_guide_from_angle"]
 
 
 class Frame(C.Structure):
@@ -40,6 +41,12 @@ class Params(C.Structure):
 class SplineFrame(C.Structure):
     _fields_ = [("H", C.c_int32), ("W", C.c_int32), ("labels", C.c_void_p), ("n_splines", C.c_int32),
                 ("n_points", C.c_int32), ("offsets", C.c_void_p), ("pts", C.c_void_p), ("guide", C.c_void_p)]
+
+
+class AdjointFrame(C.Structure):
+    _fields_ = [("H", C.c_int32), ("W", C.c_int32), ("out_rgba", C.c_void_p), ("guide", C.c_void_p),
+                ("shell", C.c_void_p), ("stall", C.c_void_p), ("grad_out", C.c_void_p), ("grad_in", C.c_void_p),
+                ("grad_phi", C.c_void_p), ("grad_mu", C.c_void_p)]
 
 
 STATS_DTYPE = np.dtype([("shells", np.int32), ("stalls", np.int32), ("status", np.int32), ("reserved", np.int32),
@@ -92,6 +99,10 @@ def lib() -> C.CDLL:
         L.gf_get_last_launch.restype = C.c_int
         L.gf_max_active_clusters.argtypes = [P, C.c_float, C.c_int]
         L.gf_max_active_clusters.restype = C.c_int
+        L.gf_fill_backward.argtypes = [P, C.c_int, C.POINTER(AdjointFrame), C.POINTER(Params), P]
+        L.gf_fill_backward.restype = C.c_int
+        L.gf_guide_from_angle.argtypes = [P, C.c_int, C.c_int, P, P, P, P, P]
+        L.gf_guide_from_angle.restype = C.c_int
         _lib = L
     return _lib
 

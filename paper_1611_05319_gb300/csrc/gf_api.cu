@@ -25,6 +25,7 @@ struct gf_ctx {
     DevBuf arena;       // fill scratch
     DevBuf garena;      // guidance scratch
     DevBuf io;          // host-buffer path device copies
+    DevBuf aarena;      // adjoint scratch
     // cached graphs of the last batched fill: gexec = preparation (descriptor
     // upload, clears, init, frame order), gexec_fill = the persistent fill kernel
     cudaGraphExec_t gexec = nullptr;
@@ -205,6 +206,12 @@ gf_status gf_create(gf_ctx **out, int device)
     ctx = new gf_ctx();
     ctx->device = device;
     ctx->sm_count = prop.multiProcessorCount;
+    e = cudaFuncSetAttribute((const void *)adj_kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    if (e != cudaSuccess) {
+        ctx->last_cuda = (int)e;
+        delete ctx;
+        return GF_ERR_CUDA;
+    }
     for (int rw : {4, 5, 8}) {
         const void *k = fill_kernel_ptr(rw);
         size_t smem = warp_smem(rw) * WARPS_PER_CTA;
@@ -229,6 +236,7 @@ void gf_destroy(gf_ctx *ctx)
     if (ctx->arena.ptr) cudaFree(ctx->arena.ptr);
     if (ctx->garena.ptr) cudaFree(ctx->garena.ptr);
     if (ctx->io.ptr) cudaFree(ctx->io.ptr);
+    if (ctx->aarena.ptr) cudaFree(ctx->aarena.ptr);
     delete ctx;
 }
 
@@ -624,6 +632,158 @@ gf_status gf_guidance_from_splines(gf_ctx *ctx, int H, int W, const uint8_t *lab
     f.H = H; f.W = W; f.labels = labels; f.n_splines = n_splines; f.n_points = n_points;
     f.offsets = offsets; f.pts = pts; f.guide = guide;
     return gf_guidance_batched(ctx, 1, &f, eta, stream);
+}
+
+gf_status gf_guide_from_angle(gf_ctx *ctx, int H, int W, const uint8_t *labels, const float *mag, const float *phi,
+                              float *guide, void *stream)
+{
+    if (!ctx || H <= 0 || W <= 0 || !labels || !mag || !phi || !guide) return GF_ERR_ARG;
+    if ((int64_t)H * W > ((int64_t)1 << 31) - 64 || ((uintptr_t)guide & 7)) return GF_ERR_ARG;
+    cudaError_t e = cudaSetDevice(ctx->device);
+    if (e != cudaSuccess) return cuda_fail(ctx, e);
+    int64_t np = (int64_t)H * W;
+    int grid = (int)std::max<int64_t>(1, std::min<int64_t>((np + 255) / 256, (int64_t)ctx->sm_count * 16));
+    angle_kernel<<<grid, 256, 0, (cudaStream_t)stream>>>(np, labels, mag, phi, (float2 *)guide);
+    CK(cudaGetLastError());
+    return GF_OK;
+}
+
+gf_status gf_fill_backward(gf_ctx *ctx, int n, const gf_adjoint_frame *frames, const gf_params *prm, void *stream)
+{
+    if (!ctx || n <= 0 || !frames) return GF_ERR_ARG;
+    gf_status s = check_params(prm);
+    if (s != GF_OK) return s;
+    if (!(prm->flags & GF_FLAG_GHOST)) return GF_ERR_UNSUPPORTED;
+    for (int i = 0; i < n; i++) {
+        const gf_adjoint_frame &f = frames[i];
+        if (f.H <= 0 || f.W <= 0 || (int64_t)f.H * f.W > ((int64_t)1 << 31) - 64) return GF_ERR_ARG;
+        if (!f.out_rgba || !f.guide || !f.shell || !f.grad_out || !f.grad_in || !f.grad_phi || !f.grad_mu)
+            return GF_ERR_ARG;
+        if (((uintptr_t)f.out_rgba & 15) || ((uintptr_t)f.grad_out & 15) || ((uintptr_t)f.grad_in & 15) ||
+            ((uintptr_t)f.guide & 7) || ((uintptr_t)f.shell & 3) || ((uintptr_t)f.grad_phi & 3) ||
+            ((uintptr_t)f.grad_mu & 3) || (f.stall && ((uintptr_t)f.stall & 3)))
+            return GF_ERR_ARG;
+    }
+    cudaError_t e = cudaSetDevice(ctx->device);
+    if (e != cudaSuccess) return cuda_fail(ctx, e);
+    cudaStream_t st = (cudaStream_t)stream;
+    std::vector<size_t> o_cnt(n), o_start(n), o_order(n);
+    size_t pos = 0;
+    std::vector<int32_t> blk(n + 1);
+    int64_t nb = 0;
+    for (int i = 0; i < n; i++) {
+        size_t np = (size_t)frames[i].H * frames[i].W;
+        o_cnt[i] = pos; pos = align_up(pos + 4 * (np + 1), 256);
+        o_start[i] = pos; pos = align_up(pos + 4 * (np + 2), 256);
+        o_order[i] = pos; pos = align_up(pos + 4 * np, 256);
+        blk[i] = (int32_t)nb;
+        nb += (int64_t)((np + 1023) / 1024);
+    }
+    blk[n] = (int32_t)nb;
+    if (nb >= INT32_MAX / 2) return GF_ERR_ARG;
+    const size_t o_K = pos; pos = align_up(pos + 4 * (size_t)n, 256);
+    const size_t o_desc = pos; pos = align_up(pos + sizeof(AdjFrameDev) * (size_t)n, 256);
+    const size_t o_blk = pos; pos = align_up(pos + 4 * (size_t)(n + 1), 256);
+    const size_t o_cur = pos; pos = align_up(pos + 4, 256);
+    // launch shape: clusters of up to 8 CTAs, one frame per cluster at a time
+    int cs = 8;
+    while (cs > 1 && cs * n > ctx->sm_count) cs >>= 1;
+    int maxc = 0;
+    {
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3(cs * 64);
+        cfg.blockDim = dim3(CTA_THREADS);
+        cudaLaunchAttribute at[1];
+        at[0].id = cudaLaunchAttributeClusterDimension;
+        at[0].val.clusterDim.x = cs;
+        at[0].val.clusterDim.y = 1;
+        at[0].val.clusterDim.z = 1;
+        cfg.attrs = at;
+        cfg.numAttrs = 1;
+        while (cs >= 1) {
+            at[0].val.clusterDim.x = cs;
+            cfg.gridDim = dim3(cs * 64);
+            if (cudaOccupancyMaxActiveClusters(&maxc, (const void *)adj_kernel, &cfg) == cudaSuccess && maxc > 0) break;
+            cudaGetLastError();
+            cs >>= 1;
+        }
+    }
+    if (maxc <= 0) return GF_ERR_UNSUPPORTED;
+    const int nc = std::max(1, std::min(maxc, n));
+    const size_t o_cf = pos; pos = align_up(pos + 8 * (size_t)nc, 256);
+    s = ensure(ctx, ctx->aarena, pos);
+    if (s != GF_OK) return s;
+    char *A = (char *)ctx->aarena.ptr;
+
+    AdjArgs aa;
+    memset(&aa, 0, sizeof(aa));
+    aa.frames = (const AdjFrameDev *)(A + o_desc);
+    aa.blk_offset = (const int32_t *)(A + o_blk);
+    aa.n_frames = n;
+    aa.mu = prm->mu;
+    aa.coef32 = (prm->mu * prm->mu) / (2.0f * prm->eps * prm->eps);
+    aa.tau = prm->snap_tau;
+    aa.frame_cursor = (int32_t *)(A + o_cur);
+    aa.cluster_frame = (int32_t *)(A + o_cf);
+    build_tab(prm->eps, aa.tab);
+
+    for (int c0 = 0; c0 < n; c0 += DESC_CHUNK) {
+        static thread_local AdjChunk ch;
+        ch.dst_frames = (AdjFrameDev *)(A + o_desc);
+        ch.dst_blk = (int32_t *)(A + o_blk);
+        ch.first = c0;
+        ch.count = std::min(DESC_CHUNK, n - c0);
+        ch.last_chunk = (c0 + ch.count == n) ? 1 : 0;
+        for (int i = 0; i < ch.count; i++) {
+            const gf_adjoint_frame &f = frames[c0 + i];
+            AdjFrameDev d;
+            d.H = f.H; d.W = f.W;
+            d.out = (const float4 *)f.out_rgba;
+            d.guide = (const float2 *)f.guide;
+            d.shell = f.shell;
+            d.stall = f.stall;
+            d.grad_out = (const float4 *)f.grad_out;
+            d.grad_in = (float4 *)f.grad_in;
+            d.grad_phi = f.grad_phi;
+            d.grad_mu = f.grad_mu;
+            d.cnt = (int32_t *)(A + o_cnt[c0 + i]);
+            d.start = (int32_t *)(A + o_start[c0 + i]);
+            d.order = (int32_t *)(A + o_order[c0 + i]);
+            d.K = (int32_t *)(A + o_K) + (c0 + i);
+            ch.frames[i] = d;
+            ch.blk[i] = blk[c0 + i];
+        }
+        ch.blk[ch.count] = blk[c0 + ch.count];
+        adj_upload_kernel<<<1, 128, 0, st>>>(ch);
+        CK(cudaGetLastError());
+    }
+    for (int i = 0; i < n; i++) {
+        size_t np = (size_t)frames[i].H * frames[i].W;
+        CK(cudaMemsetAsync(A + o_cnt[i], 0, 4 * (np + 1), st));
+        CK(cudaMemsetAsync(frames[i].grad_mu, 0, 4, st));
+    }
+    CK(cudaMemsetAsync(A + o_K, 0, 4 * (size_t)n, st));
+    CK(cudaMemsetAsync(A + o_cur, 0, 4, st));
+    const int grid = std::max(1, std::min<int>((int)std::min<int64_t>(nb * 4, INT32_MAX), ctx->sm_count * 8));
+    adj_prep_kernel<<<grid, 256, 0, st>>>(aa);
+    CK(cudaGetLastError());
+    adj_scan_kernel<<<n, 1024, 0, st>>>(aa);
+    CK(cudaGetLastError());
+    adj_scatter_kernel<<<grid, 256, 0, st>>>(aa);
+    CK(cudaGetLastError());
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)(nc * cs));
+    cfg.blockDim = dim3(CTA_THREADS);
+    cfg.stream = st;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = cs;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    CK(cudaLaunchKernelEx(&cfg, adj_kernel, aa));
+    return GF_OK;
 }
 
 gf_status gf_fill_batched_host(gf_ctx *ctx, int n, const int32_t *H, const int32_t *W,

@@ -164,4 +164,16 @@ __global__ void __launch_bounds__(256) guide_kernel(const __grid_constant__ Guid
     }
 }
 
+// g = |g| (cos phi, sin phi) at hole pixels, evaluated in FP64 and rounded once
+// (so a CPU evaluation in FP64 gives the same FP32 field).
+__global__ void __launch_bounds__(256) angle_kernel(int64_t npx, const uint8_t *labels, const float *mag,
+                                                    const float *phi, float2 *guide)
+{
+    for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < npx; p += (int64_t)gridDim.x * blockDim.x) {
+        if (__ldg(&labels[p]) != 1) continue;
+        double m = (double)__ldg(&mag[p]), a = (double)__ldg(&phi[p]);
+        guide[p] = make_float2((float)__dmul_rn(m, cos(a)), (float)__dmul_rn(m, sin(a)));
+    }
+}
+
 }  // namespace gf

@@ -127,9 +127,51 @@ struct GuideArgs {
     float eta;
 };
 
+constexpr int DESC_CHUNK = 128;  // frame descriptors per upload kernel
+
+// adjoint
+struct AdjFrameDev {
+    int32_t H, W;
+    const float4 *out;        // forward output image
+    const float2 *guide;
+    const int32_t *shell;
+    const uint32_t *stall;    // optional stall bitmap
+    const float4 *grad_out;
+    float4 *grad_in;
+    float *grad_phi;
+    float *grad_mu;           // one float per frame
+    int32_t *cnt;             // [H*W+1]: histogram, then scatter cursor
+    int32_t *start;           // [H*W+2]
+    int32_t *order;           // [H*W]
+    int32_t *K;
+};
+
+struct AdjArgs {
+    const AdjFrameDev *frames;
+    const int32_t *blk_offset;    // [n+1] first 1024-pixel block of each frame
+    int32_t n_frames;
+    float mu, coef32, tau;
+    int32_t *frame_cursor;
+    int32_t *cluster_frame;       // [2 * clusters]
+    SampleTab tab;
+};
+
+struct AdjChunk {
+    AdjFrameDev *dst_frames;
+    int32_t *dst_blk;
+    int32_t first, count, last_chunk, pad;
+    AdjFrameDev frames[DESC_CHUNK];
+    int32_t blk[DESC_CHUNK + 1];
+};
+
+__global__ void adj_upload_kernel(const __grid_constant__ AdjChunk c);
+__global__ void adj_prep_kernel(const __grid_constant__ AdjArgs a);
+__global__ void adj_scan_kernel(const __grid_constant__ AdjArgs a);
+__global__ void adj_scatter_kernel(const __grid_constant__ AdjArgs a);
+__global__ void adj_kernel(const __grid_constant__ AdjArgs a);
+
 // Descriptor upload by value through kernel parameters: no host staging buffer
 // whose lifetime would have to outlast an asynchronous copy or a graph replay.
-constexpr int DESC_CHUNK = 128;
 struct FrameChunk {
     FrameDev *dst_frames;
     int32_t *dst_cta;
@@ -153,6 +195,8 @@ const void *fill_kernel_entry(int rw);
 cudaError_t launch_fill(int rw, const cudaLaunchConfig_t &cfg, const FillParams &p);
 __global__ void init_kernel(const __grid_constant__ InitArgs a);
 __global__ void order_kernel(const FrameDev *frames, int n, int32_t *order, int32_t *cursor);
+__global__ void angle_kernel(int64_t npx, const uint8_t *labels, const float *mag, const float *phi,
+                             float2 *guide);
 __global__ void bin_kernel(const __grid_constant__ GuideArgs a, int total_points);
 __global__ void guide_kernel(const __grid_constant__ GuideArgs a);
 
