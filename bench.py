@@ -53,6 +53,8 @@ def parse():
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-plain", action="store_true")
     p.add_argument("--cpu-sample", type=int, default=24, help="frames in the oracle sample")
+    p.add_argument("--no-extra", action="store_true", help="skip the 4K rescan and adjoint legs")
+    p.add_argument("--extra-steps", type=int, default=5)
     return p.parse_args()
 
 
@@ -239,10 +241,9 @@ def main():
     clocks = clk.stop() if clk else None
     ms = t0.elapsed_time(t1) / K
     fill_ms = statistics.mean(a.elapsed_time(b) for a, b in ev_fill)
-    if dist:
-        t = torch.tensor([ms, fill_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms, fill_ms = float(t[0]), float(t[1])
+    from paper_1611_05319_gb300.shard import max_over_ranks
+    ms = max_over_ranks(ms, dist, dev)
+    fill_ms = max_over_ranks(fill_ms, dist, dev)
     st = np.frombuffer(stats.cpu().numpy().tobytes(), dtype=_lib.STATS_DTYPE)
     filled = int(st["filled"].sum())
     bad = [int(s) for s in st["status"] if s < 0]
@@ -308,15 +309,17 @@ def main():
         for _ in range(args.e2e_steps):
             se = ctx.fill_batched_host(hr, hl, None, hor, hos, splines=spl)
         w = (time.perf_counter() - w0) / args.e2e_steps
-        if dist:
-            t = torch.tensor([w], device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            w = float(t[0])
+        w = max_over_ranks(w, dist, dev)
         fe = int(se["filled"].sum())
         h2d = sum(a.nbytes + b.nbytes for a, b in zip(hr, hl)) + sum(o.nbytes + p.nbytes for o, p in spl)
         d2h = sum(a.nbytes + b.nbytes for a, b in zip(hor, hos)) + n * _lib.STATS_BYTES
         e2e = {"value": world * fe / w, "unit": "filled px/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                "ms_per_step": w * 1e3, "call": "gf_fill_batched_host (pinned host buffers, splines in)"}
+
+    extra4k = adjoint = None
+    if rank == 0 and not args.no_extra:
+        extra4k = leg_4k(ctx, dev, stream, args.extra_steps)
+        adjoint = leg_adjoint(ctx, dev, stream, args.extra_steps)
 
     if rank != 0:
         if dist:
@@ -333,11 +336,101 @@ def main():
         "frames_per_s": world * n / (ms / 1e3),
         "plain": plain, "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
         "gpu_launches": launches_per_step * K, "clocks": clocks,
+        "tracked_vs_rescan_4k": extra4k, "adjoint_16x512": adjoint,
         "status_errors": bad,
     }
     print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()
+
+
+def _time(fn, steps, stream):
+    import torch
+    fn()
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    for _ in range(steps):
+        fn()
+    b.record(stream)
+    torch.cuda.synchronize()
+    return a.elapsed_time(b) / steps
+
+
+def leg_4k(ctx, dev, stream, steps):
+    """3840x2160 frame with a 400x400 blob and bands, eps = 4: the fill kernel
+    with the tracked front against the full-image rescan of every step (the
+    kernel alone, timed with events around it)."""
+    import ctypes as C
+
+    import numpy as np
+    import torch
+
+    from paper_1611_05319_gb300 import _lib
+    from synth import configs, to_rgba
+    f = configs.frame_4k_blob()
+    H, W = f["labels"].shape
+    lab = torch.from_numpy(f["labels"]).to(dev)
+    img = torch.from_numpy(to_rgba(f["rgb"])).to(dev)
+    g = ctx.guidance(lab, f["splines"][0], f["splines"][1], 3.0)
+    shell = torch.empty((H, W), dtype=torch.int32, device=dev)
+    stats = torch.zeros((_lib.STATS_BYTES,), dtype=torch.uint8, device=dev)
+    fr = (_lib.Frame * 1)(_lib.Frame(H, W, img.data_ptr(), lab.data_ptr(), g.data_ptr(), img.data_ptr(),
+                                     shell.data_ptr(), None, None))
+    L = _lib.lib()
+    sp = C.c_void_p(stream.cuda_stream)
+    out = {}
+    for name, rescan in (("tracked", False), ("rescan", True)):
+        prm = _lib.make_params(eps=4.0, mu=50.0, c=0.05, rescan=rescan)
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        for a, b in evs:
+            a.record(stream)
+            b.record(stream)
+        for k in range(steps + 1):
+            e = evs[k - 1] if k > 0 else None
+            _lib.check(L.gf_fill_batched_ex(ctx._h, 1, fr, C.byref(prm), C.c_void_p(stats.data_ptr()), sp,
+                                            C.c_void_p(e[0].cuda_event) if e else None,
+                                            C.c_void_p(e[1].cuda_event) if e else None), "fill", ctx._h)
+        torch.cuda.synchronize()
+        ms = float(np.mean([a.elapsed_time(b) for a, b in evs]))
+        st = np.frombuffer(stats.cpu().numpy().tobytes(), dtype=_lib.STATS_DTYPE)[0]
+        out[name] = {"fill_kernel_ms": ms, "filled_px_per_s": int(st["filled"]) / (ms / 1e3),
+                     "shells": int(st["shells"]), "evaluations": int(st["evaluations"]),
+                     "launch": "cluster %d x %d" % ctx.last_launch()}
+    out["speedup_tracked_over_rescan"] = out["rescan"]["fill_kernel_ms"] / out["tracked"]["fill_kernel_ms"]
+    out["workload"] = "3840x2160, 400x400 blob + bands along 20 splines (seed 3), eps=4, mu=50, one frame"
+    return out
+
+
+def leg_adjoint(ctx, dev, stream, steps):
+    """16 frames of 512x512 (thin bands, ~5 %): forward fill and adjoint of the
+    L2 loss against the un-holed image, gradients w.r.t. colours, angle and mu."""
+    import numpy as np
+    import torch
+
+    from synth import configs, to_rgba
+    import paper_1611_05319_gb300 as gf
+    ctx = gf.Context(dev.index)
+    ctx.set_launch_config(0, 0, use_graph=False)
+    frames = configs.diff_batch(16)
+    imgs = [torch.from_numpy(to_rgba(f["gt"])).to(dev) for f in frames]
+    labs = [torch.from_numpy(f["labels"]).to(dev) for f in frames]
+    guides = ctx.guidance_batched(labs, [f["splines"][0] for f in frames], [f["splines"][1] for f in frames], 3.0)
+    state = {}
+
+    def fwd():
+        state["r"] = ctx.fill_batched(imgs, labs, guides, mu=50.0, stall=True)
+
+    def bwd():
+        ctx.fill_backward(state["r"], guides, state["go"], mu=50.0)
+
+    fms = _time(fwd, steps, stream)
+    state["go"] = [r.rgba - i for r, i in zip(state["r"], imgs)]
+    bms = _time(bwd, steps, stream)
+    filled = sum(r.stats()["filled"] for r in state["r"])
+    ctx.close()
+    return {"forward_ms": fms, "backward_ms": bms, "backward_over_forward": bms / fms, "filled_px": filled,
+            "workload": "16 x 512x512, bands ~5 %, guide from splines, eps=3, mu=50; L2 loss vs un-holed image"}
 
 
 def run_reference(args, world, rank):
