@@ -248,6 +248,19 @@ gf_status gf_fill_backward(gf_ctx *ctx, int n, const gf_adjoint_frame *frames, c
  */
 gf_status gf_set_launch_config(gf_ctx *ctx, int cluster_size, int n_clusters, int use_graph);
 
+/*
+ * Autotuner (no counterpart in the paper): fills these frames under every
+ * schedulable cluster size (1, 2, 4, 8, 16 CTAs per frame, as many persistent
+ * clusters as fit), `trials` timed runs each (CUDA events around the fill
+ * kernel), and records the fastest shape in the context for later automatic
+ * fills of frames with the same sizes, count, flags and ceil(eps).  The frames
+ * are filled by every trial.  Synchronises `stream`.  Optional outputs: the
+ * chosen cluster size and its mean fill-kernel time in ms.
+ */
+gf_status gf_autotune(gf_ctx *ctx, int n, const gf_frame *frames, const gf_params *params,
+                      gf_stats *dev_stats, void *stream, int trials, int *best_cluster_size,
+                      float *best_ms);
+
 /* Launch shape chosen by the last fill call on this context. */
 gf_status gf_get_last_launch(const gf_ctx *ctx, int *cluster_size, int *n_clusters);
 

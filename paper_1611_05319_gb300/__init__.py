@@ -95,6 +95,13 @@ class Context:
         check(lib().gf_get_last_launch(self._h, C.byref(a), C.byref(b)), "gf_get_last_launch")
         return a.value, b.value
 
+    def autotune(self, frames, stats: torch.Tensor, params, trials: int = 3, stream=None):
+        """Runs gf_autotune on prepared ctypes frames; returns (cluster_size, ms)."""
+        cs, ms = C.c_int(), C.c_float()
+        check(lib().gf_autotune(self._h, len(frames), frames, C.byref(params), _ptr(stats), _stream(stream),
+                                int(trials), C.byref(cs), C.byref(ms)), "gf_autotune", self._h)
+        return cs.value, ms.value
+
     def max_active_clusters(self, eps: float, cluster_size: int) -> int:
         return lib().gf_max_active_clusters(self._h, float(eps), int(cluster_size))
 

@@ -24,7 +24,7 @@ STATUS = {0: "ok", 1: "incomplete", -1: "invalid argument", -2: "CUDA error", -3
 EXPORTS = ["gf_create", "gf_destroy", "gf_status_string", "gf_last_cuda_error", "gf_fill",
            "gf_fill_batched", "gf_fill_batched_ex", "gf_fill_batched_host", "gf_guidance_from_splines", "gf_guidance_batched",
            "gf_set_launch_config", "gf_get_last_launch", "gf_max_active_clusters", "gf_fill_backward",
-           "gf_guide_from_angle"]
+           "gf_guide_from_angle", "gf_autotune"]
 
 
 class Frame(C.Structure):
@@ -103,6 +103,9 @@ def lib() -> C.CDLL:
         L.gf_fill_backward.restype = C.c_int
         L.gf_guide_from_angle.argtypes = [P, C.c_int, C.c_int, P, P, P, P, P]
         L.gf_guide_from_angle.restype = C.c_int
+        L.gf_autotune.argtypes = [P, C.c_int, C.POINTER(Frame), C.POINTER(Params), P, P, C.c_int,
+                                  C.POINTER(C.c_int), C.POINTER(C.c_float)]
+        L.gf_autotune.restype = C.c_int
         _lib = L
     return _lib
 

@@ -36,7 +36,33 @@ struct gf_ctx {
     int n_clusters = 0;
     int use_graph = 1;
     int last_cluster_size = 0, last_n_clusters = 0;
+    // autotuned launch shapes keyed by (n frames, H, W, eps, flags)
+    struct Tuned {
+        uint64_t key;
+        int cluster_size, n_clusters;
+        float ms;
+    };
+    std::vector<Tuned> tuned;
 };
+
+static uint64_t tune_key(int n, const gf_frame *frames, const gf_params *p)
+{
+    uint64_t h = 1469598103934665603ull;
+    for (int i = 0; i < n; i++) {
+        const uint64_t hw = ((uint64_t)(uint32_t)frames[i].H << 32) | (uint32_t)frames[i].W;
+        for (int b = 0; b < 8; b++) {
+            h ^= (hw >> (8 * b)) & 0xff;
+            h *= 1099511628211ull;
+        }
+    }
+    const uint32_t v[3] = {(uint32_t)n, p->flags, (uint32_t)std::ceil((double)p->eps)};
+    const unsigned char *c = (const unsigned char *)v;
+    for (size_t i = 0; i < sizeof(v); i++) {
+        h ^= c[i];
+        h *= 1099511628211ull;
+    }
+    return h;
+}
 
 static gf_status cuda_fail(gf_ctx *ctx, cudaError_t e)
 {
@@ -317,6 +343,15 @@ static gf_status enqueue_fill(gf_ctx *ctx, int n, const gf_frame *frames, const 
     // ---- launch shape
     const int rw = rw_for(prm->eps);
     int cs = ctx->cluster_size;
+    int tuned_nc = 0;
+    if (cs == 0) {
+        const uint64_t tk = tune_key(n, frames, prm);
+        for (const auto &t : ctx->tuned)
+            if (t.key == tk) {
+                cs = t.cluster_size;
+                tuned_nc = t.n_clusters;
+            }
+    }
     if (cs == 0) cs = (n == 1) ? 16 : 2;
     int maxc = gf_max_active_clusters(ctx, prm->eps, cs);
     while (maxc <= 0 && cs > 1) {
@@ -324,7 +359,7 @@ static gf_status enqueue_fill(gf_ctx *ctx, int n, const gf_frame *frames, const 
         maxc = gf_max_active_clusters(ctx, prm->eps, cs);
     }
     if (maxc <= 0) return GF_ERR_UNSUPPORTED;
-    int nc = ctx->n_clusters > 0 ? std::min(ctx->n_clusters, maxc) : maxc;
+    int nc = ctx->n_clusters > 0 ? std::min(ctx->n_clusters, maxc) : (tuned_nc > 0 ? std::min(tuned_nc, maxc) : maxc);
     nc = std::max(1, std::min(nc, n));
     ctx->last_cluster_size = cs;
     ctx->last_n_clusters = nc;
@@ -526,6 +561,78 @@ gf_status gf_fill_batched(gf_ctx *ctx, int n, const gf_frame *frames, const gf_p
                           gf_stats *dev_stats, void *stream)
 {
     return gf_fill_batched_ex(ctx, n, frames, params, dev_stats, stream, nullptr, nullptr);
+}
+
+/* Times the batched fill of these frames under candidate launch shapes
+ * (cluster sizes 1..16, as many clusters as fit) and keeps the fastest for
+ * later calls on frames of the same sizes and parameters.  The frames are
+ * filled (in place if out_rgba == rgba) by every trial.  Synchronises stream. */
+gf_status gf_autotune(gf_ctx *ctx, int n, const gf_frame *frames, const gf_params *params, gf_stats *dev_stats,
+                      void *stream, int trials, int *best_cluster_size, float *best_ms)
+{
+    if (!ctx || n <= 0 || !frames || !dev_stats) return GF_ERR_ARG;
+    gf_status s = check_params(params);
+    if (s != GF_OK) return s;
+    for (int i = 0; i < n; i++) {
+        s = check_frame(&frames[i]);
+        if (s != GF_OK) return s;
+    }
+    cudaError_t e = cudaSetDevice(ctx->device);
+    if (e != cudaSuccess) return cuda_fail(ctx, e);
+    cudaStream_t st = (cudaStream_t)stream;
+    if (trials <= 0) trials = 3;
+    const int save_cs = ctx->cluster_size, save_nc = ctx->n_clusters;
+    cudaEvent_t e0, e1;
+    CK(cudaEventCreate(&e0));
+    CK(cudaEventCreate(&e1));
+    int best_cs = 0, best_nc = 0;
+    float best = 1e30f;
+    for (int cs : {1, 2, 4, 8, 16}) {
+        if (gf_max_active_clusters(ctx, params->eps, cs) <= 0) continue;
+        ctx->cluster_size = cs;
+        ctx->n_clusters = 0;
+        s = enqueue_fill(ctx, n, frames, params, dev_stats, st);  // warm-up / capture
+        if (s != GF_OK) break;
+        float tot = 0.f;
+        for (int t = 0; t < trials && s == GF_OK; t++) {
+            s = enqueue_fill(ctx, n, frames, params, dev_stats, st, e0, e1);
+            if (s != GF_OK) break;
+            e = cudaEventSynchronize(e1);
+            float ms = 0.f;
+            if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+            if (e != cudaSuccess) {
+                s = cuda_fail(ctx, e);
+                break;
+            }
+            tot += ms;
+        }
+        if (s != GF_OK) break;
+        const float avg = tot / trials;
+        if (avg < best) {
+            best = avg;
+            best_cs = cs;
+            best_nc = ctx->last_n_clusters;
+        }
+    }
+    ctx->cluster_size = save_cs;
+    ctx->n_clusters = save_nc;
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (s != GF_OK) return s;
+    if (best_cs == 0) return GF_ERR_UNSUPPORTED;
+    const uint64_t tk = tune_key(n, frames, params);
+    bool found = false;
+    for (auto &t : ctx->tuned)
+        if (t.key == tk) {
+            t.cluster_size = best_cs;
+            t.n_clusters = best_nc;
+            t.ms = best;
+            found = true;
+        }
+    if (!found) ctx->tuned.push_back({tk, best_cs, best_nc, best});
+    if (best_cluster_size) *best_cluster_size = best_cs;
+    if (best_ms) *best_ms = best;
+    return GF_OK;
 }
 
 gf_status gf_fill(gf_ctx *ctx, const gf_frame *frame, const gf_params *params, gf_stats *dev_stats,

@@ -290,3 +290,36 @@ def test_batch_1080_sampled_frames_in_bench_launch():
                   stats=r.stats(), stall_steps=r.stall_steps())
         o = oracle_fill(f["rgb"], f["labels"], g)
         assert_parity(o, gg, f["labels"])
+
+
+def test_autotuned_launch_gives_identical_results():
+    import ctypes as C
+
+    import torch
+
+    import paper_1611_05319_gb300 as gf
+    from paper_1611_05319_gb300 import _lib
+    ctx = gf.Context(0)
+    cases = [_case(72, 96, 500 + i) for i in range(6)]
+    imgs = [torch.from_numpy(rgba(c[0])).cuda() for c in cases]
+    labs = [torch.from_numpy(c[1]).cuda() for c in cases]
+    gds = [torch.from_numpy(c[2]).cuda() for c in cases]
+    outs = [torch.empty_like(i) for i in imgs]
+    shells = [torch.empty(c[1].shape, dtype=torch.int32, device="cuda") for c in cases]
+    fr = (_lib.Frame * 6)()
+    for i in range(6):
+        fr[i] = _lib.Frame(72, 96, imgs[i].data_ptr(), labs[i].data_ptr(), gds[i].data_ptr(), outs[i].data_ptr(),
+                           shells[i].data_ptr(), None, None)
+    stats = torch.zeros((6 * _lib.STATS_BYTES,), dtype=torch.uint8, device="cuda")
+    prm = _lib.make_params()
+    cs, ms = ctx.autotune(fr, stats, prm, trials=1)
+    assert cs in (1, 2, 4, 8, 16) and ms > 0
+    ctx.fill_frames(fr, stats, prm)
+    torch.cuda.synchronize()
+    assert ctx.last_launch()[0] == cs
+    for i, (img, lab, g) in enumerate(cases):
+        o = oracle_fill(img, lab, g)
+        assert np.array_equal(o["shell"], shells[i].cpu().numpy())
+        filled = o["shell"] >= 0
+        assert np.abs(o["u"][filled] - outs[i].cpu().numpy()[filled]).max() <= 1e-4
+    ctx.close()
