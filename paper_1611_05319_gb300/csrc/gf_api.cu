@@ -162,9 +162,7 @@ static int rw_for(float eps)
 
 static size_t warp_smem(int rw)
 {
-    int ws = 8 + 2 * rw;
-    size_t b = (size_t)ws * ws * 16 + (size_t)ws * 4 + 64 * 4 + 8;
-    return align_up(b, 16);
+    return rw == 4 ? sizeof(WarpSmem<4>) : (rw == 5 ? sizeof(WarpSmem<5>) : sizeof(WarpSmem<8>));
 }
 
 static const void *fill_kernel_ptr(int rw) { return fill_kernel_entry(rw); }
@@ -321,7 +319,7 @@ static gf_status enqueue_fill(gf_ctx *ctx, int n, const gf_frame *frames, const 
                               cudaEvent_t ev1 = nullptr)
 {
     // ---- layout of the scratch arena
-    std::vector<size_t> off_U(n), off_Q(n), off_F(n), off_S(n);
+    std::vector<size_t> off_U(n), off_Q(n), off_F(n), off_S(n), off_L(n);
     std::vector<int> ntiles(n);
     size_t pos = 0;
     int list_cap = 1;
@@ -333,8 +331,10 @@ static gf_status enqueue_fill(gf_ctx *ctx, int n, const gf_frame *frames, const 
         off_Q[i] = pos; pos = align_up(pos + 8 * (size_t)ntiles[i], 256);
         off_F[i] = pos; pos = align_up(pos + sizeof(TileF) * 2 * (size_t)ntiles[i], 256);
         off_S[i] = pos; pos = align_up(pos + 4 * (size_t)ntiles[i], 256);
+        off_L[i] = pos; pos = align_up(pos + 4 * (size_t)ntiles[i], 256);
     }
     const size_t off_holes = pos; pos = align_up(pos + 4 * (size_t)n, 256);
+    const size_t off_icnt = pos; pos = align_up(pos + 8 * (size_t)n, 256);
     const size_t off_desc = pos; pos = align_up(pos + sizeof(FrameDev) * (size_t)n, 256);
     const size_t off_order = pos; pos = align_up(pos + 4 * (size_t)n, 256);
     const size_t off_cursor = pos; pos = align_up(pos + 4, 256);
@@ -400,6 +400,8 @@ static gf_status enqueue_fill(gf_ctx *ctx, int n, const gf_frame *frames, const 
         d.F = (TileF *)(A + off_F[i]);
         d.sched = (int32_t *)(A + off_S[i]);
         d.holes = (int32_t *)(A + off_holes) + i;
+        d.init_list = (int32_t *)(A + off_L[i]);
+        d.init_count = (int32_t *)(A + off_icnt) + 2 * i;
         hd[i] = d;
         hcta[i] = (int32_t)ctas;
         ctas += (int64_t)d.TH * ((f.W + 255) / 256);
@@ -480,6 +482,8 @@ static gf_status enqueue_fill(gf_ctx *ctx, int n, const gf_frame *frames, const 
         }
         if (e) break;
         e = cudaMemsetAsync(A + off_holes, 0, 4 * (size_t)n, stream);
+        if (e) break;
+        e = cudaMemsetAsync(A + off_icnt, 0, 8 * (size_t)n, stream);
         if (e) break;
         e = cudaMemsetAsync(A + off_ctl, 0, sizeof(GroupCtl) * (size_t)nc, stream);
         if (e) break;

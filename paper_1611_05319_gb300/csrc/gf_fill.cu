@@ -105,10 +105,12 @@ __global__ void __launch_bounds__(256) init_kernel(const __grid_constant__ InitA
         }
     }
     const int warp = t >> 5;
+    bool has_front = false;
+    int tile = 0, nq = 0;
     if (lane < 4) {
         int tx = (x0 >> 3) + warp * 4 + lane;
         if (tx < F.TW && y0 < H) {
-            int tile = ty * F.TW + tx;
+            tile = ty * F.TW + tx;
             unsigned long long u = lane == 0 ? Um[0] : lane == 1 ? Um[1] : lane == 2 ? Um[2] : Um[3];
             unsigned long long q = lane == 0 ? Qm[0] : lane == 1 ? Qm[1] : lane == 2 ? Qm[2] : Qm[3];
             F.U[tile] = u;
@@ -118,7 +120,21 @@ __global__ void __launch_bounds__(256) init_kernel(const __grid_constant__ InitA
             F.F[F.ntiles + tile].tag = INT32_MIN;
             int c = __popcll(u);
             if (c) atomicAdd(F.holes, c);
+            has_front = q != 0ull;
+            nq = __popcll(q);
         }
+    }
+    // step-0 work list: warp-aggregated append of the tiles on the initial front
+    const unsigned bm = __ballot_sync(FULL, has_front);
+    nq = __reduce_add_sync(FULL, nq);
+    if (bm) {
+        int b0 = 0;
+        if (lane == 0) {
+            b0 = atomicAdd(&F.init_count[0], __popc(bm));
+            atomicAdd(&F.init_count[1], nq);
+        }
+        b0 = __shfl_sync(FULL, b0, 0);
+        if (has_front) F.init_list[b0 + __popc(bm & ((1u << lane) - 1u))] = tile;
     }
 }
 
@@ -150,15 +166,6 @@ __global__ void order_kernel(const FrameDev *frames, int n, int32_t *order, int3
 // fill
 // ---------------------------------------------------------------------------
 enum Mode { NORMAL = 0, RESCAN = 1, STALL = 2 };
-
-template <int RW>
-struct WarpSmem {
-    static constexpr int WS = TILE + 2 * RW;
-    float4 col[WS * WS];         // colour window (cp.async)
-    uint32_t rowmask[WS];        // readable bits of the window rows
-    float tmin[64];              // per tile pixel: smallest readable weight exponent
-    unsigned long long ready;
-};
 
 __device__ __forceinline__ int nth_bit64(unsigned long long m, int q)
 {
@@ -327,6 +334,14 @@ __device__ void process_tile(const FillParams &p, const FrameDev &F, WarpSmem<RW
             if (lane == 0) ws->rowmask[r] = b;
         }
     }
+    if (MODE != STALL) {
+#pragma unroll
+        for (int h = 0; h < 2; h++) {
+            const int pix = lane + 32 * h;
+            const int gx = x0 + (pix & 7), gy = y0 + (pix >> 3);
+            if ((cand >> pix) & 1ull) ws->guide[pix] = __ldg(&F.guide[(size_t)gy * W + gx]);
+        }
+    }
     if (lane == 0) ws->ready = 0ull;
     __syncwarp();
 
@@ -368,9 +383,8 @@ __device__ void process_tile(const FillParams &p, const FrameDev &F, WarpSmem<RW
             const bool act = q < np;
             const int pix = act ? nth_bit64(P, q) : 0;
             const int px = pix & 7, py = pix >> 3;
-            const int gxp = x0 + px, gyp = y0 + py;
             float2 g = make_float2(0.f, 0.f);
-            if (act && MODE != STALL) g = __ldg(&F.guide[(size_t)gyp * W + gxp]);
+            if (act && MODE != STALL) g = ws->guide[pix];
             float ch = 1.0f, sh = 0.0f, beta = 0.0f;
             const bool rot = ghost && MODE != STALL;
             if (MODE != STALL) {
@@ -481,7 +495,7 @@ __device__ void process_tile(const FillParams &p, const FrameDev &F, WarpSmem<RW
             const int px = pix & 7, py = pix >> 3;
             const int gxp = x0 + px, gyp = y0 + py;
             float2 g = make_float2(0.f, 0.f);
-            if (act && MODE != STALL) g = __ldg(&F.guide[(size_t)gyp * W + gxp]);
+            if (act && MODE != STALL) g = ws->guide[pix];
             float ch = 1.0f, sh = 0.0f, beta = 0.0f;
             const bool rot = ghost && MODE != STALL;
             if (MODE != STALL && ghost) {
@@ -678,7 +692,6 @@ __global__ void __launch_bounds__(CTA_THREADS, 1) fill_kernel(const __grid_const
     const int cid = blockIdx.x / csize;
     GroupCtl *ctl = p.groups + cid;
     int32_t *lists = p.lists + (size_t)cid * 3 * p.list_cap;
-    const int lane = threadIdx.x & 31;
     const int gw = (threadIdx.x >> 5) * csize + crank;  // interleave CTAs
     const int nw = csize * WARPS_PER_CTA;
     const bool leader = crank == 0 && threadIdx.x == 0;
@@ -701,7 +714,6 @@ __global__ void __launch_bounds__(CTA_THREADS, 1) fill_kernel(const __grid_const
                 ctl->st_front_delta[i] = 0;
                 ctl->st_err[i] = 0;
             }
-            ctl->init_front = 0;
         }
         cluster.sync();
         const int f = __ldcg(&ctl->cur_frame[it & 1]);
@@ -710,28 +722,7 @@ __global__ void __launch_bounds__(CTA_THREADS, 1) fill_kernel(const __grid_const
         __syncthreads();
         const FrameDev &F = s_frame;
 
-        // step-0 work list: tiles holding part of the initial active boundary
-        {
-            int cnt = 0;
-            for (int base = gw * 32; base < F.ntiles; base += nw * 32) {
-                int t = base + lane;
-                unsigned long long q = (t < F.ntiles) ? __ldcg(&F.Qw[t]) : 0ull;
-                cnt += __popcll(q);
-                bool has = q != 0ull;
-                unsigned bm = __ballot_sync(FULL, has);
-                if (bm && !rescan) {
-                    int b0 = 0;
-                    if (lane == 0) b0 = atomicAdd(&ctl->list_count[0], __popc(bm));
-                    b0 = __shfl_sync(FULL, b0, 0);
-                    if (has) lists[b0 + __popc(bm & ((1u << lane) - 1u))] = t;
-                }
-            }
-            cnt = __reduce_add_sync(FULL, cnt);
-            if (lane == 0 && cnt) atomicAdd(&ctl->init_front, cnt);
-        }
-        cluster.sync();
-
-        long long n_front = __ldcg(&ctl->init_front);
+        long long n_front = __ldcg(&F.init_count[1]);
         long long filled_tot = 0, evals_tot = 0, max_front = 0;
         int stalls = 0, status = GF_OK;
         int k = 0;
@@ -752,9 +743,10 @@ __global__ void __launch_bounds__(CTA_THREADS, 1) fill_kernel(const __grid_const
             if (rescan) {
                 sweep_tiles<RW, RESCAN>(p, F, ws, ctl, lists, k, gw, nw, wc);
             } else {
+                // step 0 takes the init kernel's list, later steps the lists built by the claims
                 const int slot = k % 3;
-                const int n = __ldcg(&ctl->list_count[slot]);
-                const int32_t *L = lists + (size_t)slot * p.list_cap;
+                const int n = k == 0 ? __ldcg(&F.init_count[0]) : __ldcg(&ctl->list_count[slot]);
+                const int32_t *L = k == 0 ? F.init_list : lists + (size_t)slot * p.list_cap;
                 for (int i = gw; i < n; i += nw) {
                     int t = __ldcg(&L[i]);
                     process_tile<RW, NORMAL>(p, F, ws, ctl, lists, t, k, 0ull, wc);

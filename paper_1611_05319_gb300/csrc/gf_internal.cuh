@@ -39,6 +39,18 @@ struct SampleTab {
     int8_t cm[MAX_SAMPLES];
 };
 
+// Per-warp shared memory of the fill kernel: the staged (8 + 2 RW)^2 window
+// around one 8x8 tile.
+template <int RW>
+struct WarpSmem {
+    static constexpr int WS = TILE + 2 * RW;
+    float4 col[WS * WS];         // colour window (cp.async)
+    float2 guide[64];            // guide vectors of the tile's candidate pixels
+    uint32_t rowmask[WS];        // readable bits of the window rows
+    float tmin[64];              // per tile pixel: smallest readable weight exponent
+    unsigned long long ready;
+};
+
 struct TileF {                    // fills of one tile at one step
     unsigned long long mask;
     int32_t tag;                  // step index the mask belongs to
@@ -62,6 +74,8 @@ struct FrameDev {
     TileF *F;                     // [2][ntiles]
     int32_t *sched;               // last step the tile was scheduled for
     int32_t *holes;               // |D_h| (written by the init kernel)
+    int32_t *init_list;           // tiles holding part of d_active D^(0)_h (written by the init kernel)
+    int32_t *init_count;          // [0] tiles on init_list, [1] |d_active D^(0)_h|
 };
 
 // Per-cluster control block (global memory).  Counters are indexed by the step
@@ -76,7 +90,7 @@ struct GroupCtl {
     int32_t st_filled[2];         // stall-rule fills of step s (slot s%2)
     int32_t st_front_delta[2];
     int32_t st_err[2];
-    int32_t init_front;           // |front_0|
+    int32_t init_front_unused;
     int32_t cur_frame[2];
     int32_t pad[3];
 };
