@@ -289,21 +289,43 @@ __device__ void process_tile(const FillParams &p, const FrameDev &F, WarpSmem<RW
     const bool ghost = (p.flags & GF_FLAG_GHOST) != 0;
     const bool smart = (p.flags & GF_FLAG_SMART) != 0;
 
+    // Issue every load that depends only on the tile before using any of them:
+    // tile masks, the neighbours' fills of step k-1, the state window and the
+    // guide vectors (one L2 round trip instead of three).
     const unsigned long long U = __ldcg(&F.U[t]);
     const unsigned long long Qold = __ldcg(&F.Qw[t]);
+    int ftag = INT32_MIN;
+    unsigned long long fmsk = 0ull;
+    if (MODE == NORMAL && k > 0 && lane < 9) {
+        int nx = tx + lane % 3 - 1, ny = ty + lane / 3 - 1;
+        if (nx >= 0 && ny >= 0 && nx < F.TW && ny < F.TH) {
+            const TileF *e = &F.F[(size_t)((k - 1) & 1) * F.ntiles + (size_t)ny * F.TW + nx];
+            ftag = __ldcg(&e->tag);
+            fmsk = __ldcg(&e->mask);
+        }
+    }
+    const int wx0 = x0 - RW, wy0 = y0 - RW;
+    int32_t sv[WS];
+#pragma unroll
+    for (int r = 0; r < WS; r++) {
+        int gx = wx0 + lane, gy = wy0 + r;
+        sv[r] = (lane < WS && gx >= 0 && gy >= 0 && gx < W && gy < H) ? __ldcg(&F.shell[(size_t)gy * W + gx])
+                                                                       : SH_OUTSIDE;
+    }
+    float2 gv[2] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
+    if (MODE != STALL) {
+#pragma unroll
+        for (int h = 0; h < 2; h++) {
+            const int pix = lane + 32 * h;
+            const int gx = x0 + (pix & 7), gy = y0 + (pix >> 3);
+            if (gx < W && gy < H) gv[h] = __ldg(&F.guide[(size_t)gy * W + gx]);
+        }
+    }
+
     unsigned long long cand;
     if (MODE == NORMAL) {
         if (k > 0) {
-            unsigned long long fm = 0;
-            if (lane < 9) {
-                int nx = tx + lane % 3 - 1, ny = ty + lane / 3 - 1;
-                if (nx >= 0 && ny >= 0 && nx < F.TW && ny < F.TH) {
-                    const TileF *e = &F.F[(size_t)((k - 1) & 1) * F.ntiles + (size_t)ny * F.TW + nx];
-                    int tag = __ldcg(&e->tag);
-                    unsigned long long msk = __ldcg(&e->mask);
-                    if (tag == k - 1) fm = msk;
-                }
-            }
+            const unsigned long long fm = (ftag == k - 1) ? fmsk : 0ull;
             cand = U & dilate_nbr(fm, R + 1);
         } else {
             cand = U;
@@ -313,33 +335,22 @@ __device__ void process_tile(const FillParams &p, const FrameDev &F, WarpSmem<RW
     }
     if (cand == 0) return;
 
-    // ---- stage the window: colours asynchronously, readable bits by ballot
-    const int wx0 = x0 - RW, wy0 = y0 - RW;
+    // ---- colours of the window asynchronously; readable bits of the window by ballot
     for (int e = lane; e < WS * WS; e += 32) {
         int r = e / WS, c = e - r * WS;
         int gx = wx0 + c, gy = wy0 + r;
         if (gx >= 0 && gy >= 0 && gx < W && gy < H) cp_async16(&ws->col[e], &F.rgba[(size_t)gy * W + gx]);
     }
-    {
-        int32_t sv[WS];
 #pragma unroll
-        for (int r = 0; r < WS; r++) {
-            int gx = wx0 + lane, gy = wy0 + r;
-            sv[r] = (lane < WS && gx >= 0 && gy >= 0 && gx < W && gy < H) ? __ldcg(&F.shell[(size_t)gy * W + gx])
-                                                                           : SH_OUTSIDE;
-        }
-#pragma unroll
-        for (int r = 0; r < WS; r++) {
-            unsigned b = __ballot_sync(FULL, readable_at(sv[r], k));
-            if (lane == 0) ws->rowmask[r] = b;
-        }
+    for (int r = 0; r < WS; r++) {
+        unsigned b = __ballot_sync(FULL, readable_at(sv[r], k));
+        if (lane == 0) ws->rowmask[r] = b;
     }
     if (MODE != STALL) {
 #pragma unroll
         for (int h = 0; h < 2; h++) {
             const int pix = lane + 32 * h;
-            const int gx = x0 + (pix & 7), gy = y0 + (pix >> 3);
-            if ((cand >> pix) & 1ull) ws->guide[pix] = __ldg(&F.guide[(size_t)gy * W + gx]);
+            if ((cand >> pix) & 1ull) ws->guide[pix] = gv[h];
         }
     }
     if (lane == 0) ws->ready = 0ull;
@@ -747,9 +758,15 @@ __global__ void __launch_bounds__(CTA_THREADS, 1) fill_kernel(const __grid_const
                 const int slot = k % 3;
                 const int n = k == 0 ? __ldcg(&F.init_count[0]) : __ldcg(&ctl->list_count[slot]);
                 const int32_t *L = k == 0 ? F.init_list : lists + (size_t)slot * p.list_cap;
-                for (int i = gw; i < n; i += nw) {
-                    int t = __ldcg(&L[i]);
-                    process_tile<RW, NORMAL>(p, F, ws, ctl, lists, t, k, 0ull, wc);
+                // this warp's items are gw, gw + nw, ...; fetch 32 of them per round trip
+                for (int base = gw; base < n; base += 32 * nw) {
+                    const int idx = base + (threadIdx.x & 31) * nw;
+                    const int mine = idx < n ? __ldcg(&L[idx]) : -1;
+                    for (int q = 0; q < 32; q++) {
+                        const int t = __shfl_sync(FULL, mine, q);
+                        if (t < 0) break;
+                        process_tile<RW, NORMAL>(p, F, ws, ctl, lists, t, k, 0ull, wc);
+                    }
                 }
             }
             flush_counters<RW>(ctl, wc, k % 3, k & 1, false);
