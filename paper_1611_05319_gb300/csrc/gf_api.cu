@@ -326,7 +326,7 @@ static gf_status enqueue_fill(gf_ctx *ctx, int n, const gf_frame *frames, const 
     for (int i = 0; i < n; i++) {
         int TW = (frames[i].W + 7) / 8, TH = (frames[i].H + 7) / 8;
         ntiles[i] = TW * TH;
-        list_cap = std::max(list_cap, ntiles[i]);
+        list_cap = std::max(list_cap, 9 * ntiles[i]);  // a tile with fills reserves up to 9 slots
         off_U[i] = pos; pos = align_up(pos + 8 * (size_t)ntiles[i], 256);
         off_Q[i] = pos; pos = align_up(pos + 8 * (size_t)ntiles[i], 256);
         off_F[i] = pos; pos = align_up(pos + sizeof(TileF) * 2 * (size_t)ntiles[i], 256);

@@ -13,8 +13,8 @@
 // Front tracking.  Per step k the cluster processes a work list of tiles.  A
 // tile is on the list of step k+1 iff a pixel was filled at step k within
 // reach (ceil(eps)+1 pixels) of it; the tiles are claimed with atomicMax on a
-// per-tile step word and appended with warp-aggregated atomics (a warp-ballot
-// stream compaction).  Inside a tile only pixels within reach of a step-k fill
+// per-tile step word while list slots are reserved with one warp-aggregated
+// atomicAdd (a warp-ballot stream compaction); lost claims leave skip markers.  Inside a tile only pixels within reach of a step-k fill
 // are candidates: the only pixels whose ready test can change (new front
 // pixels are 8-neighbours of fills, and a waiting pixel's test depends only on
 // pixels of its ball).  Candidates get the exact active-boundary test from the
@@ -622,25 +622,28 @@ __device__ void process_tile(const FillParams &p, const FrameDev &F, WarpSmem<RW
         const uint32_t lowm = reach >= 8 ? 0xffu : ((1u << reach) - 1u);
         const bool nL = (colocc & lowm) != 0, nR = (colocc >> (8 - (reach >= 8 ? 8 : reach))) != 0;
         const bool nU = (rowocc & lowm) != 0, nD = (rowocc >> (8 - (reach >= 8 ? 8 : reach))) != 0;
-        bool claimed = false;
+        bool need = false;
         int nt = 0;
         if (lane < 9) {
             int dx = lane % 3 - 1, dy = lane / 3 - 1;
             int nx = tx + dx, ny = ty + dy;
-            bool need = (dx == 0 || (dx < 0 ? nL : nR)) && (dy == 0 || (dy < 0 ? nU : nD));
-            if (need && nx >= 0 && ny >= 0 && nx < F.TW && ny < F.TH) {
-                nt = ny * F.TW + nx;
-                claimed = atomicMax(&F.sched[nt], k + 1) < k + 1;
-            }
+            need = (dx == 0 || (dx < 0 ? nL : nR)) && (dy == 0 || (dy < 0 ? nU : nD)) && nx >= 0 && ny >= 0 &&
+                   nx < F.TW && ny < F.TH;
+            nt = ny * F.TW + nx;
         }
-        unsigned bm = __ballot_sync(FULL, claimed);
+        // Which neighbours to claim is known before any atomic, so the list
+        // slots are reserved while the claims are in flight; a claim lost to
+        // another tile leaves a skip marker (-1) in its slot.
+        const unsigned bm = __ballot_sync(FULL, need);
         if (bm) {
             int basei = 0;
             if (lane == 0) basei = atomicAdd(&ctl->list_count[(k + 1) % 3], __popc(bm));
+            bool claimed = false;
+            if (need) claimed = atomicMax(&F.sched[nt], k + 1) < k + 1;
             basei = __shfl_sync(FULL, basei, 0);
-            if (claimed) {
+            if (need) {
                 int pos = basei + __popc(bm & ((1u << lane) - 1u));
-                if (pos < p.list_cap) lists[(size_t)((k + 1) % 3) * p.list_cap + pos] = nt;
+                if (pos < p.list_cap) lists[(size_t)((k + 1) % 3) * p.list_cap + pos] = claimed ? nt : -1;
                 else wc.err = 1;
             }
         }
@@ -761,10 +764,11 @@ __global__ void __launch_bounds__(CTA_THREADS, 1) fill_kernel(const __grid_const
                 // this warp's items are gw, gw + nw, ...; fetch 32 of them per round trip
                 for (int base = gw; base < n; base += 32 * nw) {
                     const int idx = base + (threadIdx.x & 31) * nw;
-                    const int mine = idx < n ? __ldcg(&L[idx]) : -1;
+                    const int mine = idx < n ? __ldcg(&L[idx]) : -2;
                     for (int q = 0; q < 32; q++) {
                         const int t = __shfl_sync(FULL, mine, q);
-                        if (t < 0) break;
+                        if (t == -2) break;  // end of this warp's items
+                        if (t < 0) continue; // a claim lost to another tile
                         process_tile<RW, NORMAL>(p, F, ws, ctl, lists, t, k, 0ull, wc);
                     }
                 }
