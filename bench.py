@@ -319,8 +319,9 @@ def main():
         e2e = {"value": world * fe / w, "unit": "filled px/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                "ms_per_step": w * 1e3, "call": "gf_fill_batched_host (pinned host buffers, splines in)"}
 
-    extra4k = adjoint = None
+    extra4k = adjoint = single = None
     if rank == 0 and not args.no_extra:
+        single = leg_1080(ctx, dev, stream, max(10, args.extra_steps))
         extra4k = leg_4k(ctx, dev, stream, args.extra_steps)
         adjoint = leg_adjoint(ctx, dev, stream, args.extra_steps)
 
@@ -340,7 +341,7 @@ def main():
         "frames_per_s": world * n / (ms / 1e3),
         "plain": plain, "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
         "gpu_launches": launches_per_step * K, "clocks": clocks,
-        "tracked_vs_rescan_4k": extra4k, "adjoint_16x512": adjoint,
+        "single_1080": single, "tracked_vs_rescan_4k": extra4k, "adjoint_16x512": adjoint,
         "status_errors": bad,
     }
     print(json.dumps(line), flush=True)
@@ -359,6 +360,59 @@ def _time(fn, steps, stream):
     b.record(stream)
     torch.cuda.synchronize()
     return a.elapsed_time(b) / steps
+
+
+def leg_1080(ctx, dev, stream, steps):
+    """One 1920x1080 frame (seed 2: bands along 20 splines, 3 % holes, eps=3,
+    mu=50): guide field + fill per step, in place, one cluster."""
+    import ctypes as C
+
+    import numpy as np
+    import torch
+
+    from paper_1611_05319_gb300 import _lib
+    from synth import configs, to_rgba
+    f = configs.frame_1080()
+    H, W = f["labels"].shape
+    lab = torch.from_numpy(f["labels"]).to(dev)
+    img = torch.from_numpy(to_rgba(f["rgb"])).to(dev)
+    off = torch.from_numpy(f["splines"][0]).to(dev)
+    pts = torch.from_numpy(f["splines"][1]).to(dev)
+    g = torch.zeros((H, W, 2), dtype=torch.float32, device=dev)
+    shell = torch.empty((H, W), dtype=torch.int32, device=dev)
+    stats = torch.zeros((_lib.STATS_BYTES,), dtype=torch.uint8, device=dev)
+    fr = (_lib.Frame * 1)(_lib.Frame(H, W, img.data_ptr(), lab.data_ptr(), g.data_ptr(), img.data_ptr(),
+                                     shell.data_ptr(), None, None))
+    sf = (_lib.SplineFrame * 1)(_lib.SplineFrame(H, W, lab.data_ptr(), off.numel() - 1, pts.shape[0],
+                                                 off.data_ptr(), pts.data_ptr(), g.data_ptr()))
+    prm = _lib.make_params()
+    L = _lib.lib()
+    sp = C.c_void_p(stream.cuda_stream)
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    for a, b in evs:
+        a.record(stream)
+        b.record(stream)
+
+    def run(e=None):
+        _lib.check(L.gf_guidance_batched(ctx._h, 1, sf, C.c_float(3.0), sp), "guidance")
+        _lib.check(L.gf_fill_batched_ex(ctx._h, 1, fr, C.byref(prm), C.c_void_p(stats.data_ptr()), sp,
+                                        C.c_void_p(e[0].cuda_event) if e else None,
+                                        C.c_void_p(e[1].cuda_event) if e else None), "fill", ctx._h)
+    for _ in range(3):
+        run()
+    torch.cuda.synchronize()
+    t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    t0.record(stream)
+    for k in range(steps):
+        run(evs[k])
+    t1.record(stream)
+    torch.cuda.synchronize()
+    ms = t0.elapsed_time(t1) / steps
+    st = np.frombuffer(stats.cpu().numpy().tobytes(), dtype=_lib.STATS_DTYPE)[0]
+    return {"ms_per_frame": ms, "filled_px_per_s": int(st["filled"]) / (ms / 1e3), "frames_per_s": 1e3 / ms,
+            "fill_kernel_ms": float(np.mean([a.elapsed_time(b) for a, b in evs])), "shells": int(st["shells"]),
+            "filled_px": int(st["filled"]), "launch": "cluster %d x %d" % ctx.last_launch(),
+            "workload": "1920x1080, bands of width U[3,15] px along 20 splines, ~3 % holes (seed 2), eps=3, mu=50"}
 
 
 def leg_4k(ctx, dev, stream, steps):
