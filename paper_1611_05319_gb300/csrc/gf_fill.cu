@@ -469,20 +469,21 @@ __device__ void process_tile(const FillParams &p, const FrameDev &F, WarpSmem<RW
                     tmin = fminf(tmin, __shfl_xor_sync(FULL, tmin, o));
                 }
             }
-            bool ready;
-            if (MODE == STALL || !smart) {
-                ready = cnt > 0;
-            } else {
+            // Smart order: FP32 decision outside the guard band, FP64 re-check inside it.
+            // The group leader does the re-check; every lane then takes part in the
+            // broadcast (a full-mask shuffle must be reached by all 32 lanes).
+            bool ready = cnt > 0;
+            bool recheck = false;
+            if (MODE != STALL && smart) {
                 const float d = S_rd - p.c * S_all;
                 const float tol = 1e-3f * p.c * S_all;
-                if (d > tol) ready = true;
-                else if (d < -tol) ready = false;
-                else {
-                    ready = false;
-                    if (act && j == 0) ready = ready_fp64<RW>(p, ws, px, py, g.x, g.y, ch, sh, ghost);
-                    ready = __shfl_sync(FULL, ready, lane & ~(G - 1));
-                }
+                ready = d > tol;
+                recheck = !(d > tol) && !(d < -tol);
             }
+            bool r64 = false;
+            if (act && j == 0 && recheck) r64 = ready_fp64<RW>(p, ws, px, py, g.x, g.y, ch, sh, ghost);
+            r64 = __shfl_sync(FULL, r64, lane & ~(G - 1));
+            if (recheck) ready = r64;
             if (act && j == 0 && ready) {
                 atomicOr(&ws->ready, 1ull << pix);
                 ws->tmin[pix] = tmin;
