@@ -242,6 +242,7 @@ def main():
     if dist:
         dist.barrier()
     clocks = clk.stop() if clk else None
+    launch = "cluster %d x %d" % ctx.last_launch()
     ms = t0.elapsed_time(t1) / K
     fill_ms = statistics.mean(a.elapsed_time(b) for a, b in ev_fill)
     from paper_1611_05319_gb300.shard import max_over_ranks
@@ -335,7 +336,7 @@ def main():
         "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
         "data": "synthetic",
         "config": {"workload": WORKLOAD, "frames_per_gpu": n, "H": H, "W": W,
-                   "filled_px_per_gpu_step": filled, "launch": "cluster %d x %d" % ctx.last_launch(),
+                   "filled_px_per_gpu_step": filled, "launch": launch,
                    "autotuned_cluster_size": tuned_cs, "autotune_fill_ms": tuned_ms,
                    "l2": "inputs 2.2 GB per GPU > 129 MB L2 (no flush); the init pass streams every frame each step"},
         "frames_per_s": world * n / (ms / 1e3),
