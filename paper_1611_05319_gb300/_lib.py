@@ -18,13 +18,14 @@ GF_FLAG_SMART = 2
 GF_FLAG_RESCAN = 4
 
 STATUS = {0: "ok", 1: "incomplete", -1: "invalid argument", -2: "CUDA error", -3: "timeout",
-          -4: "no progress", -5: "out of memory", -6: "unsupported device", -7: "internal error"}
+          -4: "no progress", -5: "out of memory", -6: "unsupported device", -7: "internal error",
+          -8: "frame too large for gf_fill_noalloc"}
 
 # every function declared in include/guidefill.h
 EXPORTS = ["gf_create", "gf_destroy", "gf_status_string", "gf_last_cuda_error", "gf_fill",
            "gf_fill_batched", "gf_fill_batched_ex", "gf_fill_batched_host", "gf_guidance_from_splines", "gf_guidance_batched",
            "gf_set_launch_config", "gf_get_last_launch", "gf_max_active_clusters", "gf_fill_backward",
-           "gf_guide_from_angle", "gf_autotune"]
+           "gf_guide_from_angle", "gf_autotune", "gf_fill_noalloc"]
 
 
 class Frame(C.Structure):
@@ -106,6 +107,8 @@ def lib() -> C.CDLL:
         L.gf_autotune.argtypes = [P, C.c_int, C.POINTER(Frame), C.POINTER(Params), P, P, C.c_int,
                                   C.POINTER(C.c_int), C.POINTER(C.c_float)]
         L.gf_autotune.restype = C.c_int
+        L.gf_fill_noalloc.argtypes = [C.POINTER(Frame), C.POINTER(Params), P, P]
+        L.gf_fill_noalloc.restype = C.c_int
         _lib = L
     return _lib
 

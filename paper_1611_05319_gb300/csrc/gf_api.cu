@@ -106,7 +106,10 @@ static gf_status ensure(gf_ctx *ctx, DevBuf &b, size_t bytes)
 
 static inline size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 
-static void build_tab(float eps, SampleTab &tab)
+namespace gf {
+void build_tab(float eps, SampleTab &tab);
+}
+void gf::build_tab(float eps, SampleTab &tab)
 {
     memset(&tab, 0, sizeof(tab));
     const double e = (double)eps;
@@ -206,6 +209,7 @@ const char *gf_status_string(int s)
     case GF_ERR_OOM: return "out of device memory";
     case GF_ERR_UNSUPPORTED: return "unsupported device";
     case GF_ERR_INTERNAL: return "internal consistency check failed";
+    case GF_ERR_TOO_LARGE: return "frame larger than the fixed scratch of gf_fill_noalloc (max 4096 x 4096 px, 4194304 px)";
     default: return "unknown status";
     }
 }
