@@ -101,7 +101,7 @@ typedef struct {
     int32_t shells;      /* K: steps that filled at least one pixel */
     int32_t stalls;      /* steps filled by the stall rule */
     int32_t status;      /* gf_status of this frame */
-    int32_t reserved;
+    int32_t rechecks;    /* ready tests re-done in FP64 (implementation count) */
     int64_t filled;      /* hole pixels filled */
     int64_t evaluations; /* ready tests executed (implementation count) */
     int64_t max_front;   /* max over k of |d_active D^(k)_h| */

@@ -54,7 +54,7 @@ class FillResult:
     def stats(self) -> dict:
         """Synchronises with the device and returns the frame's gf_stats."""
         rec = np.frombuffer(self._stats_dev.cpu().numpy().tobytes(), dtype=STATS_DTYPE)[0]
-        d = {k: int(rec[k]) for k in STATS_DTYPE.names if k != "reserved"}
+        d = {k: int(rec[k]) for k in STATS_DTYPE.names}
         return d
 
     def stall_steps(self) -> np.ndarray:

@@ -50,7 +50,7 @@ class AdjointFrame(C.Structure):
                 ("grad_phi", C.c_void_p), ("grad_mu", C.c_void_p)]
 
 
-STATS_DTYPE = np.dtype([("shells", np.int32), ("stalls", np.int32), ("status", np.int32), ("reserved", np.int32),
+STATS_DTYPE = np.dtype([("shells", np.int32), ("stalls", np.int32), ("status", np.int32), ("rechecks", np.int32),
                         ("filled", np.int64), ("evaluations", np.int64), ("max_front", np.int64),
                         ("holes", np.int64)])
 STATS_BYTES = STATS_DTYPE.itemsize  # 48

@@ -226,52 +226,86 @@ __device__ __forceinline__ unsigned long long dilate_nbr(unsigned long long fm, 
     return out;
 }
 
-// FP64 confidence in the canonical sample order, the same expressions as the
-// oracle (eqs. weight, confidence); used only inside the FP32 guard band.
+// FP64 confidence of tile pixel `pix` in the canonical sample order with the
+// oracle's expressions (eqs. weight, confidence); used only inside the FP32
+// guard band.  The whole warp works on one pixel: every lane evaluates the
+// weights of its share of the samples (FP64 runs at a small fraction of the
+// FP32 rate on this part, so the exp/divide work is spread over 32 lanes),
+// then the weights are added in the canonical order exactly as the oracle
+// adds them.  Must be called by all 32 lanes.
 template <int RW>
-__device__ bool ready_fp64(const FillParams &p, const WarpSmem<RW> *ws, int px, int py, float gx, float gy,
-                           float ch, float sh, bool ghost)
+__device__ bool warp_ready_fp64(const FillParams &p, const WarpSmem<RW> *ws, int pix, bool ghost)
 {
-    double a2 = __dadd_rn(__dmul_rn((double)gx, (double)gx), __dmul_rn((double)gy, (double)gy));
-    double S_all = 0.0, S_rd = 0.0;
-    for (int s = 0; s < p.tab.ns; s++) {
-        int n = p.tab.cn[s], m = p.tab.cm[s];
-        float ox, oy;
-        if (ghost) {
-            float fn = (float)n, fm = (float)m;
-            ox = __fsub_rn(__fmul_rn(fn, ch), __fmul_rn(fm, sh));
-            oy = __fadd_rn(__fmul_rn(fn, sh), __fmul_rn(fm, ch));
-            float r = rintf(ox);
-            if (fabsf(__fsub_rn(ox, r)) <= p.tau) ox = r;
-            r = rintf(oy);
-            if (fabsf(__fsub_rn(oy, r)) <= p.tau) oy = r;
-        } else {
-            ox = (float)n;
-            oy = (float)m;
+    constexpr int NSLOT = RW == 4 ? 1 : (RW == 5 ? 2 : 5);  // ceil(samples / 32) for ceil(eps) = 3, 4, 7
+    const int lane = threadIdx.x & 31;
+    const int px = pix & 7, py = pix >> 3;
+    const float gx = ws->guide[pix].x, gy = ws->guide[pix].y;
+    float ch = 1.0f, sh = 0.0f;
+    if (ghost) {
+        const float a2f = __fadd_rn(__fmul_rn(gx, gx), __fmul_rn(gy, gy));
+        const float a = __fsqrt_rn(a2f);
+        if (a > 0.0f) {
+            ch = __fdiv_rn(gx, a);
+            sh = __fdiv_rn(gy, a);
         }
-        float flx = floorf(ox), fly = floorf(oy);
-        float frx = __fsub_rn(ox, flx), fry = __fsub_rn(oy, fly);
-        int ix = px + RW + (int)flx, iy = py + RW + (int)fly;
-        uint32_t need = frx > 0.0f ? 3u : 1u;
-        bool ok = ((ws->rowmask[iy] >> ix) & need) == need;
-        if (fry > 0.0f) ok = ok && (((ws->rowmask[iy + 1] >> ix) & need) == need);
-        double t;
-        if (ghost) {
-            t = __dmul_rn(__dmul_rn(p.coef64, a2), (double)(m * m));
-        } else {
-            double proj = __dadd_rn(__dmul_rn(-(double)gy, (double)n), __dmul_rn((double)gx, (double)m));
-            t = __dmul_rn(__dmul_rn(p.coef64, proj), proj);
-        }
-        double w = __ddiv_rn(exp(-t), __dsqrt_rn((double)(n * n + m * m)));
-        S_all = __dadd_rn(S_all, w);
-        if (ok) S_rd = __dadd_rn(S_rd, w);
     }
-    double C = __ddiv_rn(S_rd, S_all);
-    return C > p.c64;
+    const double a2 = __dadd_rn(__dmul_rn((double)gx, (double)gx), __dmul_rn((double)gy, (double)gy));
+    double w[NSLOT];
+    int ok[NSLOT];
+#pragma unroll
+    for (int q = 0; q < NSLOT; q++) {
+        const int s = q * 32 + lane;
+        w[q] = 0.0;
+        ok[q] = 0;
+        if (s < p.tab.ns) {
+            const int n = p.tab.cn[s], m = p.tab.cm[s];
+            float ox, oy;
+            if (ghost) {
+                const float fn = (float)n, fm = (float)m;
+                ox = __fsub_rn(__fmul_rn(fn, ch), __fmul_rn(fm, sh));
+                oy = __fadd_rn(__fmul_rn(fn, sh), __fmul_rn(fm, ch));
+                float r = rintf(ox);
+                if (fabsf(__fsub_rn(ox, r)) <= p.tau) ox = r;
+                r = rintf(oy);
+                if (fabsf(__fsub_rn(oy, r)) <= p.tau) oy = r;
+            } else {
+                ox = (float)n;
+                oy = (float)m;
+            }
+            const float flx = floorf(ox), fly = floorf(oy);
+            const float frx = __fsub_rn(ox, flx), fry = __fsub_rn(oy, fly);
+            const int ix = px + RW + (int)flx, iy = py + RW + (int)fly;
+            const uint32_t need = frx > 0.0f ? 3u : 1u;
+            bool rd = ((ws->rowmask[iy] >> ix) & need) == need;
+            if (fry > 0.0f) rd = rd && (((ws->rowmask[iy + 1] >> ix) & need) == need);
+            double t;
+            if (ghost) {
+                t = __dmul_rn(__dmul_rn(p.coef64, a2), (double)(m * m));
+            } else {
+                const double proj = __dadd_rn(__dmul_rn(-(double)gy, (double)n), __dmul_rn((double)gx, (double)m));
+                t = __dmul_rn(__dmul_rn(p.coef64, proj), proj);
+            }
+            w[q] = __ddiv_rn(exp(-t), __dsqrt_rn((double)(n * n + m * m)));
+            ok[q] = rd ? 1 : 0;
+        }
+    }
+    double S_all = 0.0, S_rd = 0.0;
+#pragma unroll
+    for (int q = 0; q < NSLOT; q++) {
+        for (int src = 0; src < 32; src++) {
+            const double wv = __shfl_sync(FULL, w[q], src);
+            const int okv = __shfl_sync(FULL, ok[q], src);
+            if (q * 32 + src < p.tab.ns) {
+                S_all = __dadd_rn(S_all, wv);
+                if (okv) S_rd = __dadd_rn(S_rd, wv);
+            }
+        }
+    }
+    return __ddiv_rn(S_rd, S_all) > p.c64;
 }
 
 struct WarpCounters {
-    int filled, delta, evals, err;
+    int filled, delta, evals, err, rechecks;
 };
 
 // Processes one tile at step k (one warp).  Returns nothing; updates counters.
@@ -353,7 +387,10 @@ __device__ void process_tile(const FillParams &p, const FrameDev &F, WarpSmem<RW
             if ((cand >> pix) & 1ull) ws->guide[pix] = gv[h];
         }
     }
-    if (lane == 0) ws->ready = 0ull;
+    if (lane == 0) {
+        ws->ready = 0ull;
+        ws->recheck = 0ull;
+    }
     __syncwarp();
 
     // ---- exact active-boundary test of the candidates
@@ -472,23 +509,32 @@ __device__ void process_tile(const FillParams &p, const FrameDev &F, WarpSmem<RW
             // Smart order: FP32 decision outside the guard band, FP64 re-check inside it.
             // The group leader does the re-check; every lane then takes part in the
             // broadcast (a full-mask shuffle must be reached by all 32 lanes).
+            // Smart order: decided in FP32 outside a guard band around c, re-checked in
+            // FP64 inside it.  Band: relative 1e-4 for the rotated ball, where the FP32
+            // error of both sums is below ~1e-5 relative (the m = 0 terms are exact and
+            // the error of each other term is bounded by t e^-t <= 1/e times a few ulp);
+            // 1e-3 for the lattice ball, whose projection g_perp.(n, m) can cancel.
             bool ready = cnt > 0;
             bool recheck = false;
             if (MODE != STALL && smart) {
                 const float d = S_rd - p.c * S_all;
-                const float tol = 1e-3f * p.c * S_all;
+                const float tol = (ghost ? 1e-4f : 1e-3f) * p.c * S_all;
                 ready = d > tol;
                 recheck = !(d > tol) && !(d < -tol);
             }
-            bool r64 = false;
-            if (act && j == 0 && recheck) r64 = ready_fp64<RW>(p, ws, px, py, g.x, g.y, ch, sh, ghost);
-            r64 = __shfl_sync(FULL, r64, lane & ~(G - 1));
-            if (recheck) ready = r64;
-            if (act && j == 0 && ready) {
-                atomicOr(&ws->ready, 1ull << pix);
+            if (act && j == 0 && (ready || recheck)) {
+                atomicOr(recheck ? &ws->recheck : &ws->ready, 1ull << pix);
                 ws->tmin[pix] = tmin;
             }
         }
+    }
+    __syncwarp();
+    // FP64 re-checks, one pixel at a time with the whole warp
+    for (unsigned long long rc = ws->recheck; rc; rc &= rc - 1ull) {
+        const int pix = __ffsll((long long)rc) - 1;
+        const bool r64 = warp_ready_fp64<RW>(p, ws, pix, ghost);
+        if (lane == 0 && r64) atomicOr(&ws->ready, 1ull << pix);
+        wc.rechecks++;
     }
     cp_async_wait_all();
     __syncwarp();
@@ -656,7 +702,7 @@ __device__ __forceinline__ void flush_counters(GroupCtl *ctl, const WarpCounters
                                                bool stall)
 {
     const int lane = threadIdx.x & 31;
-    int f = wc.filled, d = wc.delta, e = wc.evals, er = wc.err;
+    int f = wc.filled, d = wc.delta, e = wc.evals, er = wc.err, rc = wc.rechecks;
     // all lanes hold identical values except err (per lane)
     er = __reduce_or_sync(FULL, er);
     if (lane == 0) {
@@ -665,6 +711,7 @@ __device__ __forceinline__ void flush_counters(GroupCtl *ctl, const WarpCounters
             if (d) atomicAdd(&ctl->front_delta[slot3], d);
             if (e) atomicAdd(&ctl->evals[slot3], e);
             if (er) atomicOr(&ctl->err[slot3], er);
+            if (rc) atomicAdd(&ctl->rechecks, rc);
         } else {
             if (f) atomicAdd(&ctl->st_filled[slot2], f);
             if (d) atomicAdd(&ctl->st_front_delta[slot2], d);
@@ -729,6 +776,7 @@ __global__ void __launch_bounds__(CTA_THREADS, 1) fill_kernel(const __grid_const
                 ctl->st_front_delta[i] = 0;
                 ctl->st_err[i] = 0;
             }
+            ctl->rechecks = 0;
         }
         cluster.sync();
         const int f = __ldcg(&ctl->cur_frame[it & 1]);
@@ -754,7 +802,7 @@ __global__ void __launch_bounds__(CTA_THREADS, 1) fill_kernel(const __grid_const
                 ctl->st_front_delta[k & 1] = 0;
                 ctl->st_err[k & 1] = 0;
             }
-            WarpCounters wc = {0, 0, 0, 0};
+            WarpCounters wc = {0, 0, 0, 0, 0};
             if (rescan) {
                 sweep_tiles<RW, RESCAN>(p, F, ws, ctl, lists, k, gw, nw, wc);
             } else {
@@ -789,7 +837,7 @@ __global__ void __launch_bounds__(CTA_THREADS, 1) fill_kernel(const __grid_const
             if (filled == 0) {
                 if (n_front == 0) break;  // Algorithm 1: D^(k) exhausted (or the rest unreachable)
                 // stall rule: no front pixel is ready; fill the front isotropically
-                WarpCounters ws2 = {0, 0, 0, 0};
+                WarpCounters ws2 = {0, 0, 0, 0, 0};
                 sweep_tiles<RW, STALL>(p, F, ws, ctl, lists, k, gw, nw, ws2);
                 flush_counters<RW>(ctl, ws2, k % 3, k & 1, true);
                 cluster.sync();
@@ -820,7 +868,7 @@ __global__ void __launch_bounds__(CTA_THREADS, 1) fill_kernel(const __grid_const
             st.evaluations = evals_tot;
             st.max_front = max_front;
             st.holes = holes;
-            st.reserved = 0;
+            st.rechecks = __ldcg(&ctl->rechecks);
             if (status == GF_OK && filled_tot < holes) status = GF_INCOMPLETE;
             st.status = status;
             *F.stats = st;

@@ -49,6 +49,7 @@ struct WarpSmem {
     uint32_t rowmask[WS];        // readable bits of the window rows
     float tmin[64];              // per tile pixel: smallest readable weight exponent
     unsigned long long ready;
+    unsigned long long recheck;   // pixels whose ready test is re-done in FP64
 };
 
 struct TileF {                    // fills of one tile at one step
@@ -90,7 +91,7 @@ struct GroupCtl {
     int32_t st_filled[2];         // stall-rule fills of step s (slot s%2)
     int32_t st_front_delta[2];
     int32_t st_err[2];
-    int32_t init_front_unused;
+    int32_t rechecks;             // FP64 re-checks of the current frame (statistics only)
     int32_t cur_frame[2];
     int32_t pad[3];
 };
