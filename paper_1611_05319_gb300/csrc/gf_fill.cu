@@ -524,7 +524,7 @@ __device__ void process_tile(const FillParams &p, const FrameDev &F, WarpSmem<RW
             }
             if (act && j == 0 && (ready || recheck)) {
                 atomicOr(recheck ? &ws->recheck : &ws->ready, 1ull << pix);
-                ws->tmin[pix] = tmin;
+                ws->rot[pix] = make_float4(ch, sh, beta, tmin);
             }
         }
     }
@@ -541,6 +541,53 @@ __device__ void process_tile(const FillParams &p, const FrameDev &F, WarpSmem<RW
     const unsigned long long Rm = ws->ready;
     const int nr = __popcll(Rm);
 
+    // ---- tile bookkeeping and neighbour claims, issued before the colour pass so
+    //      that their round trips overlap it
+    const unsigned long long Qnew = (Qold & ~cand) | (P & ~Rm);
+    if (lane == 0) {
+        if (Rm) {
+            F.U[t] = U & ~Rm;
+            TileF *e = &F.F[(size_t)(k & 1) * F.ntiles + t];
+            e->mask = Rm;
+            e->tag = k;
+        }
+        if (Qnew != Qold) F.Qw[t] = Qnew;
+    }
+    wc.filled += nr;
+    wc.delta += __popcll(Qnew) - __popcll(Qold);
+    // Tiles for step k+1: the neighbours within reach of this step's fills.  Which
+    // neighbours to claim is known before any atomic, so the list slots are reserved
+    // while the claims (atomicMax on the tile's step word) are in flight; a claim
+    // lost to another tile leaves a skip marker (-1) in its slot.
+    bool need = false;
+    int nt = 0, basei = 0, oldsched = 0;
+    unsigned bm = 0u;
+    if (MODE != RESCAN && Rm) {
+        const int reach = R + 1;
+        uint32_t colocc = 0, rowocc = 0;
+#pragma unroll
+        for (int y = 0; y < 8; y++) {
+            uint32_t bt = (uint32_t)((Rm >> (8 * y)) & 0xffu);
+            colocc |= bt;
+            if (bt) rowocc |= 1u << y;
+        }
+        const uint32_t lowm = reach >= 8 ? 0xffu : ((1u << reach) - 1u);
+        const bool nL = (colocc & lowm) != 0, nR = (colocc >> (8 - (reach >= 8 ? 8 : reach))) != 0;
+        const bool nU = (rowocc & lowm) != 0, nD = (rowocc >> (8 - (reach >= 8 ? 8 : reach))) != 0;
+        if (lane < 9) {
+            int dx = lane % 3 - 1, dy = lane / 3 - 1;
+            int nx = tx + dx, ny = ty + dy;
+            need = (dx == 0 || (dx < 0 ? nL : nR)) && (dy == 0 || (dy < 0 ? nU : nD)) && nx >= 0 && ny >= 0 &&
+                   nx < F.TW && ny < F.TH;
+            nt = ny * F.TW + nx;
+        }
+        bm = __ballot_sync(FULL, need);
+        if (bm) {
+            if (lane == 0) basei = atomicAdd(&ctl->list_count[(k + 1) % 3], __popc(bm));
+            if (need) oldsched = atomicMax(&F.sched[nt], k + 1);
+        }
+    }
+
     // ---- fill the ready pixels: normalised weighted average of bilinear ghost values
     if (nr) {
         const int G = nr <= 4 ? 8 : (nr <= 8 ? 4 : (nr <= 16 ? 2 : 1));
@@ -554,18 +601,9 @@ __device__ void process_tile(const FillParams &p, const FrameDev &F, WarpSmem<RW
             const int gxp = x0 + px, gyp = y0 + py;
             float2 g = make_float2(0.f, 0.f);
             if (act && MODE != STALL) g = ws->guide[pix];
-            float ch = 1.0f, sh = 0.0f, beta = 0.0f;
             const bool rot = ghost && MODE != STALL;
-            if (MODE != STALL && ghost) {
-                float a2 = __fadd_rn(__fmul_rn(g.x, g.x), __fmul_rn(g.y, g.y));
-                float a = __fsqrt_rn(a2);
-                if (a > 0.0f) {
-                    ch = __fdiv_rn(g.x, a);
-                    sh = __fdiv_rn(g.y, a);
-                }
-                beta = p.coef32 * a2;
-            }
-            const float tmin = act ? ws->tmin[pix] : 0.f;
+            const float4 rt = act ? ws->rot[pix] : make_float4(1.f, 0.f, 0.f, 0.f);
+            const float ch = rt.x, sh = rt.y, beta = rt.z, tmin = rt.w;
             float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
             float wsum = 0.f;
             if (act) {
@@ -642,57 +680,14 @@ __device__ void process_tile(const FillParams &p, const FrameDev &F, WarpSmem<RW
         }
     }
 
-    // ---- tile bookkeeping
-    const unsigned long long Qnew = (Qold & ~cand) | (P & ~Rm);
-    if (lane == 0) {
-        if (Rm) {
-            F.U[t] = U & ~Rm;
-            TileF *e = &F.F[(size_t)(k & 1) * F.ntiles + t];
-            e->mask = Rm;
-            e->tag = k;
-        }
-        if (Qnew != Qold) F.Qw[t] = Qnew;
-    }
-    wc.filled += nr;
-    wc.delta += __popcll(Qnew) - __popcll(Qold);
 
-    // ---- schedule neighbour tiles for step k+1 (warp-aggregated append)
-    if (MODE != RESCAN && Rm) {
-        const int reach = R + 1;
-        uint32_t colocc = 0, rowocc = 0;
-#pragma unroll
-        for (int y = 0; y < 8; y++) {
-            uint32_t bt = (uint32_t)((Rm >> (8 * y)) & 0xffu);
-            colocc |= bt;
-            if (bt) rowocc |= 1u << y;
-        }
-        const uint32_t lowm = reach >= 8 ? 0xffu : ((1u << reach) - 1u);
-        const bool nL = (colocc & lowm) != 0, nR = (colocc >> (8 - (reach >= 8 ? 8 : reach))) != 0;
-        const bool nU = (rowocc & lowm) != 0, nD = (rowocc >> (8 - (reach >= 8 ? 8 : reach))) != 0;
-        bool need = false;
-        int nt = 0;
-        if (lane < 9) {
-            int dx = lane % 3 - 1, dy = lane / 3 - 1;
-            int nx = tx + dx, ny = ty + dy;
-            need = (dx == 0 || (dx < 0 ? nL : nR)) && (dy == 0 || (dy < 0 ? nU : nD)) && nx >= 0 && ny >= 0 &&
-                   nx < F.TW && ny < F.TH;
-            nt = ny * F.TW + nx;
-        }
-        // Which neighbours to claim is known before any atomic, so the list
-        // slots are reserved while the claims are in flight; a claim lost to
-        // another tile leaves a skip marker (-1) in its slot.
-        const unsigned bm = __ballot_sync(FULL, need);
-        if (bm) {
-            int basei = 0;
-            if (lane == 0) basei = atomicAdd(&ctl->list_count[(k + 1) % 3], __popc(bm));
-            bool claimed = false;
-            if (need) claimed = atomicMax(&F.sched[nt], k + 1) < k + 1;
-            basei = __shfl_sync(FULL, basei, 0);
-            if (need) {
-                int pos = basei + __popc(bm & ((1u << lane) - 1u));
-                if (pos < p.list_cap) lists[(size_t)((k + 1) % 3) * p.list_cap + pos] = claimed ? nt : -1;
-                else wc.err = 1;
-            }
+    // ---- list entries of the claims (their atomics have returned by now)
+    if (bm) {
+        basei = __shfl_sync(FULL, basei, 0);
+        if (need) {
+            const int pos = basei + __popc(bm & ((1u << lane) - 1u));
+            if (pos < p.list_cap) lists[(size_t)((k + 1) % 3) * p.list_cap + pos] = oldsched < k + 1 ? nt : -1;
+            else wc.err = 1;
         }
     }
 }
@@ -766,6 +761,7 @@ __global__ void __launch_bounds__(CTA_THREADS, 1) fill_kernel(const __grid_const
             ctl->cur_frame[it & 1] = f;
             for (int i = 0; i < 3; i++) {
                 ctl->list_count[i] = 0;
+                ctl->cursor[i] = 0;
                 ctl->filled[i] = 0;
                 ctl->front_delta[i] = 0;
                 ctl->evals[i] = 0;
@@ -790,9 +786,14 @@ __global__ void __launch_bounds__(CTA_THREADS, 1) fill_kernel(const __grid_const
         int stalls = 0, status = GF_OK;
         int k = 0;
         const int max_shells = F.max_shells;
+        // the length and the first item of the current step's work list are loaded
+        // ahead, together with the previous step's counters
+        int n_cur = __ldcg(&F.init_count[0]);
+        int t0_cur = gw < n_cur ? __ldcg(&F.init_list[gw]) : -1;
         for (;;) {
             if (leader) {
                 const int s1 = (k + 1) % 3;
+                ctl->cursor[s1] = 0;
                 ctl->filled[s1] = 0;
                 ctl->front_delta[s1] = 0;
                 ctl->evals[s1] = 0;
@@ -808,26 +809,42 @@ __global__ void __launch_bounds__(CTA_THREADS, 1) fill_kernel(const __grid_const
             } else {
                 // step 0 takes the init kernel's list, later steps the lists built by the claims
                 const int slot = k % 3;
-                const int n = k == 0 ? __ldcg(&F.init_count[0]) : __ldcg(&ctl->list_count[slot]);
+                const int n = n_cur;
                 const int32_t *L = k == 0 ? F.init_list : lists + (size_t)slot * p.list_cap;
-                // this warp's items are gw, gw + nw, ...; fetch 32 of them per round trip
-                for (int base = gw; base < n; base += 32 * nw) {
-                    const int idx = base + (threadIdx.x & 31) * nw;
-                    const int mine = idx < n ? __ldcg(&L[idx]) : -2;
-                    for (int q = 0; q < 32; q++) {
-                        const int t = __shfl_sync(FULL, mine, q);
-                        if (t == -2) break;  // end of this warp's items
-                        if (t < 0) continue; // a claim lost to another tile
-                        process_tile<RW, NORMAL>(p, F, ws, ctl, lists, t, k, 0ull, wc);
+                // Item gw goes to warp gw; items beyond the warp count are handed out
+                // by a per-step cursor (the next grab is in flight while a tile is
+                // processed), so uneven tiles do not leave warps idle at the barrier.
+                // Negative items are claims lost to another tile.
+                const bool lane0 = (threadIdx.x & 31) == 0;
+                const bool more = n > nw;
+                int pre = 0;
+                if (lane0 && more) pre = atomicAdd(&ctl->cursor[slot], 1);
+                const int t0 = gw < n ? t0_cur : -1;
+                if (t0 >= 0) process_tile<RW, NORMAL>(p, F, ws, ctl, lists, t0, k, 0ull, wc);
+                if (more) {
+                    int nxt = nw + __shfl_sync(FULL, pre, 0);
+                    while (nxt < n) {
+                        const int t = __ldcg(&L[nxt]);
+                        if (lane0) pre = atomicAdd(&ctl->cursor[slot], 1);
+                        if (t >= 0) process_tile<RW, NORMAL>(p, F, ws, ctl, lists, t, k, 0ull, wc);
+                        nxt = nw + __shfl_sync(FULL, pre, 0);
                     }
                 }
             }
             flush_counters<RW>(ctl, wc, k % 3, k & 1, false);
             cluster.sync();
+            // one round trip: this step's counters and the next step's list
+            const int s3n = (k + 1) % 3;
+            const int32_t *Ln = lists + (size_t)s3n * p.list_cap;
             const int filled = __ldcg(&ctl->filled[k % 3]);
-            n_front += __ldcg(&ctl->front_delta[k % 3]);
-            evals_tot += __ldcg(&ctl->evals[k % 3]);
-            if (__ldcg(&ctl->err[k % 3])) {
+            const int dlt = __ldcg(&ctl->front_delta[k % 3]);
+            const int ev = __ldcg(&ctl->evals[k % 3]);
+            const int er = __ldcg(&ctl->err[k % 3]);
+            int n_next = __ldcg(&ctl->list_count[s3n]);
+            int t0_next = gw < p.list_cap ? __ldcg(&Ln[gw]) : -1;  // used only if gw < n_next
+            n_front += dlt;
+            evals_tot += ev;
+            if (er) {
                 status = GF_ERR_INTERNAL;
                 break;
             }
@@ -851,8 +868,13 @@ __global__ void __launch_bounds__(CTA_THREADS, 1) fill_kernel(const __grid_const
                 stalls++;
                 fk = sf;
                 if (leader && F.stall_bits) atomicOr(&F.stall_bits[k >> 5], 1u << (k & 31));
+                // the stall fills appended claims to the next step's list
+                n_next = __ldcg(&ctl->list_count[s3n]);
+                t0_next = gw < p.list_cap ? __ldcg(&Ln[gw]) : -1;
             }
             filled_tot += fk;
+            n_cur = n_next;
+            t0_cur = t0_next;
             k++;
             if (k >= max_shells) {
                 status = GF_ERR_NO_PROGRESS;

@@ -47,7 +47,7 @@ struct WarpSmem {
     float4 col[WS * WS];         // colour window (cp.async)
     float2 guide[64];            // guide vectors of the tile's candidate pixels
     uint32_t rowmask[WS];        // readable bits of the window rows
-    float tmin[64];              // per tile pixel: smallest readable weight exponent
+    float4 rot[64];              // per ready pixel: unit guide (c, s), weight scale beta, smallest readable exponent
     unsigned long long ready;
     unsigned long long recheck;   // pixels whose ready test is re-done in FP64
 };
@@ -84,6 +84,7 @@ struct FrameDev {
 // cluster may still read it.
 struct GroupCtl {
     int32_t list_count[3];        // work list consumed by step s lives in slot s%3
+    int32_t cursor[3];            // hand-out cursor of the items of step s beyond the warp count
     int32_t filled[3];            // fills of step s (normal evaluation)
     int32_t front_delta[3];       // net change of the front size during step s
     int32_t evals[3];
