@@ -242,7 +242,7 @@ gf_status gf_create(gf_ctx **out, int device)
     }
     for (int rw : {4, 5, 8}) {
         const void *k = fill_kernel_ptr(rw);
-        size_t smem = warp_smem(rw) * WARPS_PER_CTA;
+        size_t smem = warp_smem(rw) * fill_warps(rw);
         e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e == cudaSuccess) e = cudaFuncSetAttribute(k, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
         if (e != cudaSuccess) {
@@ -299,8 +299,8 @@ int gf_max_active_clusters(gf_ctx *ctx, float eps, int cluster_size)
     int rw = rw_for(eps);
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(cluster_size * 64);
-    cfg.blockDim = dim3(CTA_THREADS);
-    cfg.dynamicSmemBytes = warp_smem(rw) * WARPS_PER_CTA;
+    cfg.blockDim = dim3(32 * fill_warps(rw));
+    cfg.dynamicSmemBytes = warp_smem(rw) * fill_warps(rw);
     cudaLaunchAttribute at[1];
     at[0].id = cudaLaunchAttributeClusterDimension;
     at[0].val.clusterDim.x = cluster_size;
@@ -454,8 +454,8 @@ static gf_status enqueue_fill(gf_ctx *ctx, int n, const gf_frame *frames, const 
 
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((unsigned)(nc * cs));
-    cfg.blockDim = dim3(CTA_THREADS);
-    cfg.dynamicSmemBytes = warp_smem(rw) * WARPS_PER_CTA;
+    cfg.blockDim = dim3(32 * fill_warps(rw));
+    cfg.dynamicSmemBytes = warp_smem(rw) * fill_warps(rw);
     cfg.stream = stream;
     cudaLaunchAttribute at[1];
     at[0].id = cudaLaunchAttributeClusterDimension;
@@ -662,13 +662,14 @@ gf_status gf_guidance_batched(gf_ctx *ctx, int n, const gf_spline_frame *frames,
     cudaError_t e = cudaSetDevice(ctx->device);
     if (e != cudaSuccess) return cuda_fail(ctx, e);
     cudaStream_t st = (cudaStream_t)stream;
-    std::vector<size_t> off_cnt(n), off_list(n);
+    std::vector<size_t> off_cnt(n), off_list(n), off_seg(n);
     size_t pos = 0;
     int64_t tot_pts = 0, tot_bins = 0;
     for (int i = 0; i < n; i++) {
         int NBX = (frames[i].W + BIN - 1) / BIN, NBY = (frames[i].H + BIN - 1) / BIN;
         off_cnt[i] = pos; pos = align_up(pos + 4 * (size_t)NBX * NBY, 256);
         off_list[i] = pos; pos = align_up(pos + 4 * (size_t)NBX * NBY * BIN_CAP, 256);
+        off_seg[i] = pos; pos = align_up(pos + 64 * (size_t)std::max(frames[i].n_points, 1), 256);
         tot_pts += frames[i].n_points;
         tot_bins += (int64_t)NBX * NBY;
     }
@@ -695,6 +696,7 @@ gf_status gf_guidance_batched(gf_ctx *ctx, int n, const gf_spline_frame *frames,
         d.guide = (float2 *)f.guide;
         d.bin_count = (int32_t *)(A + off_cnt[i]);
         d.bin_list = (int32_t *)(A + off_list[i]);
+        d.seg64 = (double *)(A + off_seg[i]);
         hd[i] = d;
         hpo[i] = (int32_t)pp; hbo[i] = (int32_t)bb;
         pp += f.n_points;

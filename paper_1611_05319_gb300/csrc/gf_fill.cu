@@ -692,26 +692,32 @@ __device__ void process_tile(const FillParams &p, const FrameDev &F, WarpSmem<RW
     }
 }
 
-template <int RW>
-__device__ __forceinline__ void flush_counters(GroupCtl *ctl, const WarpCounters &wc, int slot3, int slot2,
-                                               bool stall)
+// Adds a warp's counters of step k to slot k%3.  With `clear_next`, lane 0 of
+// the first warp of each CTA also clears the slot of step k+1 and the work-list
+// count of step k+2: their last readers passed the barrier of step k-1 and
+// their next writers start after the barrier of step k.
+__device__ __forceinline__ void flush_counters(GroupCtl *ctl, const WarpCounters &wc, int k, bool stall,
+                                               bool clear_next)
 {
     const int lane = threadIdx.x & 31;
+    const int s = k % 3;
     int f = wc.filled, d = wc.delta, e = wc.evals, er = wc.err, rc = wc.rechecks;
     // all lanes hold identical values except err (per lane)
     er = __reduce_or_sync(FULL, er);
     if (lane == 0) {
-        if (!stall) {
-            if (f) atomicAdd(&ctl->filled[slot3], f);
-            if (d) atomicAdd(&ctl->front_delta[slot3], d);
-            if (e) atomicAdd(&ctl->evals[slot3], e);
-            if (er) atomicOr(&ctl->err[slot3], er);
-            if (rc) atomicAdd(&ctl->rechecks, rc);
-        } else {
-            if (f) atomicAdd(&ctl->st_filled[slot2], f);
-            if (d) atomicAdd(&ctl->st_front_delta[slot2], d);
-            if (e) atomicAdd(&ctl->evals[slot3], e);
-            if (er) atomicOr(&ctl->st_err[slot2], er);
+        if (f) atomicAdd(&ctl->filled[s], f);
+        if (d) atomicAdd(&ctl->front_delta[s], d);
+        if (e && !stall) atomicAdd(&ctl->evals[s], e);  // Sigma_k |front_k| counts the evaluation pass only
+        if (er) atomicOr(&ctl->err[s], er);
+        if (rc) atomicAdd(&ctl->rechecks, rc);
+        if (clear_next) {
+            const int s1 = (k + 1) % 3;
+            ctl->cursor[s1] = 0;
+            ctl->filled[s1] = 0;
+            ctl->front_delta[s1] = 0;
+            ctl->evals[s1] = 0;
+            ctl->err[s1] = 0;
+            ctl->list_count[(k + 2) % 3] = 0;
         }
     }
 }
@@ -738,7 +744,7 @@ __device__ void sweep_tiles(const FillParams &p, const FrameDev &F, WarpSmem<RW>
 }
 
 template <int RW>
-__global__ void __launch_bounds__(CTA_THREADS, 1) fill_kernel(const __grid_constant__ FillParams p)
+__global__ void __launch_bounds__(fill_warps(RW) * 32, 1) fill_kernel(const __grid_constant__ FillParams p)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ FrameDev s_frame;
@@ -750,7 +756,7 @@ __global__ void __launch_bounds__(CTA_THREADS, 1) fill_kernel(const __grid_const
     GroupCtl *ctl = p.groups + cid;
     int32_t *lists = p.lists + (size_t)cid * 3 * p.list_cap;
     const int gw = (threadIdx.x >> 5) * csize + crank;  // interleave CTAs
-    const int nw = csize * WARPS_PER_CTA;
+    const int nw = csize * fill_warps(RW);
     const bool leader = crank == 0 && threadIdx.x == 0;
     const bool rescan = (p.flags & GF_FLAG_RESCAN) != 0;
 
@@ -766,11 +772,6 @@ __global__ void __launch_bounds__(CTA_THREADS, 1) fill_kernel(const __grid_const
                 ctl->front_delta[i] = 0;
                 ctl->evals[i] = 0;
                 ctl->err[i] = 0;
-            }
-            for (int i = 0; i < 2; i++) {
-                ctl->st_filled[i] = 0;
-                ctl->st_front_delta[i] = 0;
-                ctl->st_err[i] = 0;
             }
             ctl->rechecks = 0;
         }
@@ -791,24 +792,12 @@ __global__ void __launch_bounds__(CTA_THREADS, 1) fill_kernel(const __grid_const
         int n_cur = __ldcg(&F.init_count[0]);
         int t0_cur = gw < n_cur ? __ldcg(&F.init_list[gw]) : -1;
         for (;;) {
-            if (leader) {
-                const int s1 = (k + 1) % 3;
-                ctl->cursor[s1] = 0;
-                ctl->filled[s1] = 0;
-                ctl->front_delta[s1] = 0;
-                ctl->evals[s1] = 0;
-                ctl->err[s1] = 0;
-                ctl->list_count[(k + 2) % 3] = 0;
-                ctl->st_filled[k & 1] = 0;
-                ctl->st_front_delta[k & 1] = 0;
-                ctl->st_err[k & 1] = 0;
-            }
+            const int slot = k % 3;
             WarpCounters wc = {0, 0, 0, 0, 0};
             if (rescan) {
                 sweep_tiles<RW, RESCAN>(p, F, ws, ctl, lists, k, gw, nw, wc);
             } else {
                 // step 0 takes the init kernel's list, later steps the lists built by the claims
-                const int slot = k % 3;
                 const int n = n_cur;
                 const int32_t *L = k == 0 ? F.init_list : lists + (size_t)slot * p.list_cap;
                 // Item gw goes to warp gw; items beyond the warp count are handed out
@@ -831,46 +820,51 @@ __global__ void __launch_bounds__(CTA_THREADS, 1) fill_kernel(const __grid_const
                     }
                 }
             }
-            flush_counters<RW>(ctl, wc, k % 3, k & 1, false);
+            flush_counters(ctl, wc, k, false, threadIdx.x < 32);
             cluster.sync();
             // one round trip: this step's counters and the next step's list
             const int s3n = (k + 1) % 3;
             const int32_t *Ln = lists + (size_t)s3n * p.list_cap;
-            const int filled = __ldcg(&ctl->filled[k % 3]);
-            const int dlt = __ldcg(&ctl->front_delta[k % 3]);
-            const int ev = __ldcg(&ctl->evals[k % 3]);
-            const int er = __ldcg(&ctl->err[k % 3]);
+            const int filled = __ldcg(&ctl->filled[slot]);
+            const int dlt = __ldcg(&ctl->front_delta[slot]);
+            const int ev = __ldcg(&ctl->evals[slot]);
+            const int er = __ldcg(&ctl->err[slot]);
             int n_next = __ldcg(&ctl->list_count[s3n]);
             int t0_next = gw < p.list_cap ? __ldcg(&Ln[gw]) : -1;  // used only if gw < n_next
-            n_front += dlt;
             evals_tot += ev;
             if (er) {
                 status = GF_ERR_INTERNAL;
                 break;
             }
-            long long front_k = n_front + filled;
+            long long front_k = n_front + dlt + filled;
             if (front_k > max_front) max_front = front_k;
             int fk = filled;
             if (filled == 0) {
-                if (n_front == 0) break;  // Algorithm 1: D^(k) exhausted (or the rest unreachable)
-                // stall rule: no front pixel is ready; fill the front isotropically
+                if (n_front + dlt == 0) break;  // Algorithm 1: D^(k) exhausted (or the rest unreachable)
+                // stall rule: no front pixel is ready; fill the front isotropically.  The
+                // stall pass adds to the same slot (its counters were zero after the
+                // evaluation pass, except the front delta).
                 WarpCounters ws2 = {0, 0, 0, 0, 0};
                 sweep_tiles<RW, STALL>(p, F, ws, ctl, lists, k, gw, nw, ws2);
-                flush_counters<RW>(ctl, ws2, k % 3, k & 1, true);
+                flush_counters(ctl, ws2, k, true, false);
                 cluster.sync();
-                const int sf = __ldcg(&ctl->st_filled[k & 1]);
-                n_front += __ldcg(&ctl->st_front_delta[k & 1]);
-                if (__ldcg(&ctl->st_err[k & 1])) {
+                const int sf = __ldcg(&ctl->filled[slot]);
+                const int dlt2 = __ldcg(&ctl->front_delta[slot]);
+                const int er2 = __ldcg(&ctl->err[slot]);
+                // the stall fills appended claims to the next step's list
+                n_next = __ldcg(&ctl->list_count[s3n]);
+                t0_next = gw < p.list_cap ? __ldcg(&Ln[gw]) : -1;
+                if (er2) {
                     status = GF_ERR_INTERNAL;
                     break;
                 }
                 if (sf == 0) break;  // front pixels with no readable sample at all
+                n_front += dlt2;
                 stalls++;
                 fk = sf;
                 if (leader && F.stall_bits) atomicOr(&F.stall_bits[k >> 5], 1u << (k & 31));
-                // the stall fills appended claims to the next step's list
-                n_next = __ldcg(&ctl->list_count[s3n]);
-                t0_next = gw < p.list_cap ? __ldcg(&Ln[gw]) : -1;
+            } else {
+                n_front += dlt;
             }
             filled_tot += fk;
             n_cur = n_next;

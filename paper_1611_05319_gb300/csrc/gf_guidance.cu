@@ -62,6 +62,21 @@ __global__ void __launch_bounds__(256) bin_kernel(const __grid_constant__ GuideA
     float vx = __fsub_rn(B.x, A.x), vy = __fsub_rn(B.y, A.y);
     float l2 = __fadd_rn(__fmul_rn(vx, vx), __fmul_rn(vy, vy));
     if (!(l2 > 0.0f)) return;
+    {
+        // FP64 terms of this segment used by every pixel that picks it (same
+        // expressions as a per-pixel evaluation, computed once)
+        const double ax = A.x, ay = A.y;
+        const double dvx = __dsub_rn((double)B.x, ax), dvy = __dsub_rn((double)B.y, ay);
+        const double len = __dsqrt_rn(__dadd_rn(__dmul_rn(dvx, dvx), __dmul_rn(dvy, dvy)));
+        double *s = F.seg64 + 8 * (size_t)i;
+        s[0] = ax;
+        s[1] = ay;
+        s[2] = dvx;
+        s[3] = dvy;
+        s[4] = __dmul_rn(len, len);
+        s[5] = __ddiv_rn(dvx, len);
+        s[6] = __ddiv_rn(dvy, len);
+    }
     float grow = 3.0f * a.eta + 1.0f;
     float xmin = fminf(A.x, B.x) - grow, xmax = fmaxf(A.x, B.x) + grow;
     float ymin = fminf(A.y, B.y) - grow, ymax = fmaxf(A.y, B.y) + grow;
@@ -93,11 +108,14 @@ __global__ void __launch_bounds__(256) guide_kernel(const __grid_constant__ Guid
 {
     __shared__ float4 seg[BIN_CAP];
     __shared__ int segid[BIN_CAP];
+    __shared__ short holes_s[BIN * BIN];
+    __shared__ int nholes;
     const int gb = blockIdx.x;
     const int f = find_frame(a.bin_offset, a.n_frames, gb);
     const SplineFrameDev &F = a.frames[f];
     const int b = gb - __ldg(&a.bin_offset[f]);
     const int bx = b % F.NBX, by = b / F.NBX;
+    if (threadIdx.x == 0) nholes = 0;
     const int cnt = __ldcg(&F.bin_count[b]);
     const bool overflow = cnt > BIN_CAP;
     const int nloc = overflow ? 0 : cnt;
@@ -108,15 +126,27 @@ __global__ void __launch_bounds__(256) guide_kernel(const __grid_constant__ Guid
         segid[s] = i;
     }
     __syncthreads();
+    // compact the bin's hole pixels so that the FP64 work below runs in full warps
+    for (int e0 = 0; e0 < BIN * BIN; e0 += blockDim.x) {
+        const int e = e0 + threadIdx.x;
+        const int x = bx * BIN + (e & (BIN - 1)), y = by * BIN + (e >> 5);
+        const bool h = x < F.W && y < F.H && __ldg(&F.labels[(size_t)y * F.W + x]) == 1;
+        const unsigned m = __ballot_sync(0xffffffffu, h);
+        int base = 0;
+        if ((threadIdx.x & 31) == 0 && m) base = atomicAdd(&nholes, __popc(m));
+        base = __shfl_sync(0xffffffffu, base, 0);
+        if (h) holes_s[base + __popc(m & ((1u << (threadIdx.x & 31)) - 1u))] = (short)e;
+    }
+    __syncthreads();
+    const int nh = nholes;
     const float t3 = 3.0f * a.eta;
     const float thr = __fmul_rn(t3, t3);
-    const double eta = (double)a.eta;
-    for (int e = threadIdx.x; e < BIN * BIN; e += blockDim.x) {
-        int x = bx * BIN + (e & (BIN - 1)), y = by * BIN + (e >> 5);
-        if (x >= F.W || y >= F.H) continue;
-        size_t p = (size_t)y * F.W + x;
-        if (__ldg(&F.labels[p]) != 1) continue;
-        float px = (float)x, py = (float)y;
+    const double den = __dmul_rn(__dmul_rn(2.0, (double)a.eta), (double)a.eta);
+    for (int q = threadIdx.x; q < nh; q += blockDim.x) {
+        const int e = holes_s[q];
+        const int x = bx * BIN + (e & (BIN - 1)), y = by * BIN + (e >> 5);
+        const size_t p = (size_t)y * F.W + x;
+        const float px = (float)x, py = (float)y;
         float best = INFINITY;
         int bi = 0x7fffffff;
         if (!overflow) {
@@ -146,19 +176,18 @@ __global__ void __launch_bounds__(256) guide_kernel(const __grid_constant__ Guid
         }
         float2 out = make_float2(0.0f, 0.0f);
         if (bi != 0x7fffffff && best <= thr) {
-            float2 A = __ldg(&F.pts[bi]), B = __ldg(&F.pts[bi + 1]);
-            double ax = A.x, ay = A.y, bxx = B.x, byy = B.y;
-            double vx = __dsub_rn(bxx, ax), vy = __dsub_rn(byy, ay);
-            double len = __dsqrt_rn(__dadd_rn(__dmul_rn(vx, vx), __dmul_rn(vy, vy)));
-            double wx = __dsub_rn((double)x, ax), wy = __dsub_rn((double)y, ay);
-            double t = __ddiv_rn(__dadd_rn(__dmul_rn(wx, vx), __dmul_rn(wy, vy)), __dmul_rn(len, len));
+            const double *s = F.seg64 + 8 * (size_t)bi;
+            const double ax = __ldcg(&s[0]), ay = __ldcg(&s[1]), vx = __ldcg(&s[2]), vy = __ldcg(&s[3]);
+            const double len2 = __ldcg(&s[4]), tx = __ldcg(&s[5]), ty = __ldcg(&s[6]);
+            const double wx = __dsub_rn((double)x, ax), wy = __dsub_rn((double)y, ay);
+            double t = __ddiv_rn(__dadd_rn(__dmul_rn(wx, vx), __dmul_rn(wy, vy)), len2);
             if (t < 0.0) t = 0.0;
             if (t > 1.0) t = 1.0;
-            double qx = __dsub_rn(wx, __dmul_rn(t, vx)), qy = __dsub_rn(wy, __dmul_rn(t, vy));
-            double d2 = __dadd_rn(__dmul_rn(qx, qx), __dmul_rn(qy, qy));
-            double ev = exp(__ddiv_rn(-d2, __dmul_rn(__dmul_rn(2.0, eta), eta)));
-            out.x = (float)__dmul_rn(__ddiv_rn(vx, len), ev);
-            out.y = (float)__dmul_rn(__ddiv_rn(vy, len), ev);
+            const double qx = __dsub_rn(wx, __dmul_rn(t, vx)), qy = __dsub_rn(wy, __dmul_rn(t, vy));
+            const double d2 = __dadd_rn(__dmul_rn(qx, qx), __dmul_rn(qy, qy));
+            const double ev = exp(__ddiv_rn(-d2, den));
+            out.x = (float)__dmul_rn(tx, ev);
+            out.y = (float)__dmul_rn(ty, ev);
         }
         F.guide[p] = out;
     }

@@ -13,6 +13,10 @@ constexpr int MAX_SAMPLES = 224;     // lattice points with n^2+m^2 <= 64, minus
 constexpr int MAX_R = 8;             // ceil(eps) <= 8
 constexpr int WARPS_PER_CTA = 16;
 constexpr int CTA_THREADS = WARPS_PER_CTA * 32;
+// Warps per CTA of the fill kernel: 16, or 12 for the 24x24 window (eps > 4),
+// whose state-window loads need more than the 128 registers a thread gets at
+// 16 warps.
+__host__ __device__ constexpr int fill_warps(int rw) { return rw == 8 ? 12 : 16; }
 
 // Per-pixel state word (out_shell): readable at step k  <=>  (uint)(s+1) < (uint)(k+1)
 constexpr int32_t SH_KNOWN = -1;
@@ -83,15 +87,15 @@ struct FrameDev {
 // that writes them (mod 3) so that no counter is reset while another CTA of the
 // cluster may still read it.
 struct GroupCtl {
+    // Per-step counters live in slot s%3 for step s.  During step s the slot of
+    // step s+1 (and the work-list count of step s+2) is cleared, so a slot is
+    // never cleared while a warp of the cluster may still read it.
     int32_t list_count[3];        // work list consumed by step s lives in slot s%3
     int32_t cursor[3];            // hand-out cursor of the items of step s beyond the warp count
-    int32_t filled[3];            // fills of step s (normal evaluation)
+    int32_t filled[3];            // fills of step s (evaluation pass, then stall pass if any)
     int32_t front_delta[3];       // net change of the front size during step s
-    int32_t evals[3];
+    int32_t evals[3];             // front pixels evaluated at step s (evaluation pass only)
     int32_t err[3];
-    int32_t st_filled[2];         // stall-rule fills of step s (slot s%2)
-    int32_t st_front_delta[2];
-    int32_t st_err[2];
     int32_t rechecks;             // FP64 re-checks of the current frame (statistics only)
     int32_t cur_frame[2];
     int32_t pad[3];
@@ -133,6 +137,7 @@ struct SplineFrameDev {
     float2 *guide;
     int32_t *bin_count;  // [NBX*NBY]
     int32_t *bin_list;   // [NBX*NBY*BIN_CAP]
+    double *seg64;       // [n_points][8]: per segment start a, v = b - a, |v|^2 (as |v|*|v|), v/|v| (FP64)
 };
 
 struct GuideArgs {

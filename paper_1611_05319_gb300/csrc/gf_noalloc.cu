@@ -93,7 +93,7 @@ int rw_of(float eps)
 
 size_t smem_of(int rw)
 {
-    return WARPS_PER_CTA * (rw == 4 ? sizeof(WarpSmem<4>) : (rw == 5 ? sizeof(WarpSmem<5>) : sizeof(WarpSmem<8>)));
+    return fill_warps(rw) * (rw == 4 ? sizeof(WarpSmem<4>) : (rw == 5 ? sizeof(WarpSmem<5>) : sizeof(WarpSmem<8>)));
 }
 
 // Once per device, with that device current: the scratch's device address and
@@ -115,7 +115,7 @@ cudaError_t setup_device(int dev)
         for (int cs = 16; cs >= 1 && best == 0; cs >>= 1) {
             cudaLaunchConfig_t cfg = {};
             cfg.gridDim = dim3(cs);
-            cfg.blockDim = dim3(CTA_THREADS);
+            cfg.blockDim = dim3(32 * fill_warps(rws[i]));
             cfg.dynamicSmemBytes = smem_of(rws[i]);
             cudaLaunchAttribute at[1];
             at[0].id = cudaLaunchAttributeClusterDimension;
@@ -240,7 +240,7 @@ extern "C" gf_status gf_fill_noalloc(const gf_frame *f, const gf_params *p, gf_s
     if (cudaGetLastError() != cudaSuccess) return GF_ERR_CUDA;
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((unsigned)cs);
-    cfg.blockDim = dim3(CTA_THREADS);
+    cfg.blockDim = dim3(32 * fill_warps(rw));
     cfg.dynamicSmemBytes = smem_of(rw);
     cfg.stream = st;
     cudaLaunchAttribute at[1];
