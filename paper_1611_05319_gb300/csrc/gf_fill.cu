@@ -308,15 +308,45 @@ struct WarpCounters {
     int filled, delta, evals, err, rechecks;
 };
 
-// Processes one tile at step k (one warp).  Returns nothing; updates counters.
+// Neighbour-tile claims made by a warp's last tile: the list slots are written
+// once their atomics have returned, i.e. after the warp has issued the loads of
+// its next tile (or before the step's counter flush).
+struct PendingClaims {
+    unsigned bm;  // lanes (< 9) holding a claim, 0 if none
+    int base;     // lane 0: first reserved list slot
+    int old;      // per lane: the claimed tile's previous step word
+    int nt;       // per lane: the claimed tile
+    int k;        // step the claims were made at
+};
+
+__device__ __forceinline__ void write_claims(const FillParams &p, int32_t *lists, PendingClaims &pc, WarpCounters &wc)
+{
+    if (pc.bm) {  // warp-uniform
+        const int lane = threadIdx.x & 31;
+        const int base = __shfl_sync(FULL, pc.base, 0);
+        if ((pc.bm >> lane) & 1u) {
+            const int pos = base + __popc(pc.bm & ((1u << lane) - 1u));
+            if (pos < p.list_cap) lists[(size_t)((pc.k + 1) % 3) * p.list_cap + pos] = pc.old < pc.k + 1 ? pc.nt : -1;
+            else wc.err = 1;
+        }
+        pc.bm = 0u;
+    }
+}
+
+// Processes one tile at step k (one warp): candidates, exact front test, ready
+// test and fill in one pass over each front pixel's samples, tile masks, claims
+// of the neighbour tiles for step k+1.
 template <int RW, int MODE>
 __device__ void process_tile(const FillParams &p, const FrameDev &F, WarpSmem<RW> *ws, GroupCtl *ctl,
-                             int32_t *lists, int t, int k, unsigned long long cand_in, WarpCounters &wc)
+                             int32_t *lists, int t, int k, unsigned long long cand_in, WarpCounters &wc,
+                             PendingClaims &pc)
 {
     constexpr int WS = WarpSmem<RW>::WS;
     const int lane = threadIdx.x & 31;
     const int W = F.W, H = F.H;
-    __syncwarp();  // the previous tile's shared-memory reads are complete
+    // the previous tile's shared-memory reads and window copies are complete
+    cp_async_wait_all();
+    __syncwarp();
     const int tx = t % F.TW, ty = t / F.TW;
     const int x0 = tx * TILE, y0 = ty * TILE;
     const int R = p.tab.R;
@@ -324,16 +354,20 @@ __device__ void process_tile(const FillParams &p, const FrameDev &F, WarpSmem<RW
     const bool smart = (p.flags & GF_FLAG_SMART) != 0;
 
     // Issue every load that depends only on the tile before using any of them:
-    // tile masks, the neighbours' fills of step k-1, the state window and the
-    // guide vectors (one L2 round trip instead of three).
+    // tile masks, the neighbours' step-(k-1) fills and hole masks, the state
+    // window, the guide vectors and (speculatively) the colour window.
     const unsigned long long U = __ldcg(&F.U[t]);
     const unsigned long long Qold = __ldcg(&F.Qw[t]);
     int ftag = INT32_MIN;
-    unsigned long long fmsk = 0ull;
-    if (MODE == NORMAL && k > 0 && lane < 9) {
-        int nx = tx + lane % 3 - 1, ny = ty + lane / 3 - 1;
-        if (nx >= 0 && ny >= 0 && nx < F.TW && ny < F.TH) {
-            const TileF *e = &F.F[(size_t)((k - 1) & 1) * F.ntiles + (size_t)ny * F.TW + nx];
+    unsigned long long fmsk = 0ull, unb = 0ull;
+    const int ndx = lane % 3 - 1, ndy = lane / 3 - 1;
+    const int nxt_x = tx + ndx, nxt_y = ty + ndy;
+    const bool nvalid = lane < 9 && nxt_x >= 0 && nxt_y >= 0 && nxt_x < F.TW && nxt_y < F.TH;
+    const int nt = nxt_y * F.TW + nxt_x;
+    if (MODE != RESCAN && nvalid) {
+        unb = __ldcg(&F.U[nt]);
+        if (MODE == NORMAL && k > 0) {
+            const TileF *e = &F.F[(size_t)((k - 1) & 1) * F.ntiles + nt];
             ftag = __ldcg(&e->tag);
             fmsk = __ldcg(&e->mask);
         }
@@ -355,6 +389,13 @@ __device__ void process_tile(const FillParams &p, const FrameDev &F, WarpSmem<RW
             if (gx < W && gy < H) gv[h] = __ldg(&F.guide[(size_t)gy * W + gx]);
         }
     }
+    for (int e = lane; e < WS * WS; e += 32) {
+        int r = e / WS, c = e - r * WS;
+        int gx = wx0 + c, gy = wy0 + r;
+        if (gx >= 0 && gy >= 0 && gx < W && gy < H) cp_async16(&ws->col[e], &F.rgba[(size_t)gy * W + gx]);
+    }
+    // the previous tile's claims have returned by now
+    write_claims(p, lists, pc, wc);
 
     unsigned long long cand;
     if (MODE == NORMAL) {
@@ -369,12 +410,7 @@ __device__ void process_tile(const FillParams &p, const FrameDev &F, WarpSmem<RW
     }
     if (cand == 0) return;
 
-    // ---- colours of the window asynchronously; readable bits of the window by ballot
-    for (int e = lane; e < WS * WS; e += 32) {
-        int r = e / WS, c = e - r * WS;
-        int gx = wx0 + c, gy = wy0 + r;
-        if (gx >= 0 && gy >= 0 && gx < W && gy < H) cp_async16(&ws->col[e], &F.rgba[(size_t)gy * W + gx]);
-    }
+    // ---- readable bits of the window by ballot; guide vectors of the candidates
 #pragma unroll
     for (int r = 0; r < WS; r++) {
         unsigned b = __ballot_sync(FULL, readable_at(sv[r], k));
@@ -421,11 +457,21 @@ __device__ void process_tile(const FillParams &p, const FrameDev &F, WarpSmem<RW
     const int np = __popcll(P);
     wc.evals += np;
 
-    // ---- ready test (eqs. weight, confidence, ready), G lanes per pixel
+    // ---- ready test (eqs. weight, confidence, ready) and the fill value in one
+    //      pass over the samples, G lanes per front pixel.  Each lane keeps its
+    //      colour sum relative to the smallest weight exponent it has read (the
+    //      normalisation cancels in the average and keeps e^-t from underflowing);
+    //      the G partial sums are brought to the group's smallest exponent when
+    //      they are combined.
     if (np) {
+        cp_async_wait_all();
+        __syncwarp();
         const int G = np <= 4 ? 8 : (np <= 8 ? 4 : (np <= 16 ? 2 : 1));
         const int per = 32 / G;
         const int j = lane & (G - 1), grp = lane / G;
+        const int ns = p.tab.ns;
+        const bool rot = ghost && MODE != STALL;
+        const bool iso = ghost || MODE == STALL;  // the exponent depends on |m| only
         for (int base = 0; base < np; base += per) {
             const int q = base + grp;
             const bool act = q < np;
@@ -434,7 +480,6 @@ __device__ void process_tile(const FillParams &p, const FrameDev &F, WarpSmem<RW
             float2 g = make_float2(0.f, 0.f);
             if (act && MODE != STALL) g = ws->guide[pix];
             float ch = 1.0f, sh = 0.0f, beta = 0.0f;
-            const bool rot = ghost && MODE != STALL;
             if (MODE != STALL) {
                 float a2 = __fadd_rn(__fmul_rn(g.x, g.x), __fmul_rn(g.y, g.y));
                 if (ghost) {
@@ -446,15 +491,13 @@ __device__ void process_tile(const FillParams &p, const FrameDev &F, WarpSmem<RW
                     beta = p.coef32 * a2;
                 }
             }
-            float S_rd = 0.f, S_all = 0.f, tmin = INFINITY;
+            float S_rd = 0.f, S_all = 0.f, tmin = INFINITY, wsum = 0.f;
+            float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
             int cnt = 0;
-            for (int gi = 0; gi <= R; gi++) {
-                const float mm = (float)(gi * gi);
-                const float tg = beta * mm;
-                const float eg = (ghost || MODE == STALL) ? expf(-tg) : 0.f;
-                float accg = 0.f;
-                for (int s = p.tab.m_start[gi] + j; s < p.tab.m_start[gi + 1]; s += G) {
-                    const float nf = p.tab.n_f[s], mf = p.tab.m_f[s];
+            if (act) {
+#pragma unroll 2
+                for (int s = j; s < ns; s += G) {
+                    const float nf = p.tab.n_f[s], mf = p.tab.m_f[s], invd = p.tab.invd[s];
                     float ox, oy;
                     if (rot) {
                         ox = __fsub_rn(__fmul_rn(nf, ch), __fmul_rn(mf, sh));
@@ -473,42 +516,70 @@ __device__ void process_tile(const FillParams &p, const FrameDev &F, WarpSmem<RW
                     const uint32_t need = frx > 0.0f ? 3u : 1u;
                     bool ok = ((ws->rowmask[iy] >> ix) & need) == need;
                     if (fry > 0.0f) ok = ok && (((ws->rowmask[iy + 1] >> ix) & need) == need);
-                    if (ghost || MODE == STALL) {
-                        if (ok) {
-                            accg += p.tab.invd[s];
-                            cnt++;
-                            tmin = fminf(tmin, tg);
-                        }
+                    float tt;
+                    if (iso) {
+                        tt = beta * (mf * mf);
                     } else {
-                        // lattice ball: weight exponent per sample
-                        float proj = -g.y * nf + g.x * mf;
-                        float ts = p.coef32 * proj * proj;
-                        float w = expf(-ts) * p.tab.invd[s];
-                        S_all += w;
-                        if (ok) {
-                            S_rd += w;
-                            cnt++;
-                            tmin = fminf(tmin, ts);
+                        const float proj = -g.y * nf + g.x * mf;  // lattice ball: g_perp . (n, m)
+                        tt = p.coef32 * proj * proj;
+                    }
+                    const float w0 = expf(-tt) * invd;
+                    S_all += w0;
+                    if (ok) {
+                        S_rd += w0;
+                        cnt++;
+                        if (tt < tmin) {
+                            const float sc = expf(tt - tmin);  // 0 for the first readable sample
+                            acc.x *= sc; acc.y *= sc; acc.z *= sc; acc.w *= sc;
+                            wsum *= sc;
+                            tmin = tt;
                         }
+                        const float w = expf(tmin - tt) * invd;
+                        const float4 *cb = &ws->col[iy * WS + ix];
+                        const float4 v = cb[0];
+                        const float l00 = (1.f - frx) * (1.f - fry);
+                        float4 val = make_float4(l00 * v.x, l00 * v.y, l00 * v.z, l00 * v.w);
+                        if (frx > 0.f) {
+                            const float l = frx * (1.f - fry);
+                            const float4 c1 = cb[1];
+                            val.x += l * c1.x; val.y += l * c1.y; val.z += l * c1.z; val.w += l * c1.w;
+                        }
+                        if (fry > 0.f) {
+                            const float l = (1.f - frx) * fry;
+                            const float4 c2 = cb[WS];
+                            val.x += l * c2.x; val.y += l * c2.y; val.z += l * c2.z; val.w += l * c2.w;
+                            if (frx > 0.f) {
+                                const float l3 = frx * fry;
+                                const float4 c3 = cb[WS + 1];
+                                val.x += l3 * c3.x; val.y += l3 * c3.y; val.z += l3 * c3.z; val.w += l3 * c3.w;
+                            }
+                        }
+                        acc.x += w * val.x; acc.y += w * val.y; acc.z += w * val.z; acc.w += w * val.w;
+                        wsum += w;
                     }
                 }
-                if (ghost || MODE == STALL) {
-                    S_rd += eg * accg;
-                    S_all += eg * p.tab.Dm[gi] * (j == 0 ? 1.f : 0.f);
-                }
             }
+            // combine the G lanes of a pixel
+            float tg = tmin;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1)
+                if (o < G) tg = fminf(tg, __shfl_xor_sync(FULL, tg, o));
+            const float sc = (tmin == INFINITY) ? 0.f : expf(tg - tmin);
+            acc.x *= sc; acc.y *= sc; acc.z *= sc; acc.w *= sc;
+            wsum *= sc;
 #pragma unroll
             for (int o = 1; o < 32; o <<= 1) {
                 if (o < G) {
                     S_rd += __shfl_xor_sync(FULL, S_rd, o);
                     S_all += __shfl_xor_sync(FULL, S_all, o);
                     cnt += __shfl_xor_sync(FULL, cnt, o);
-                    tmin = fminf(tmin, __shfl_xor_sync(FULL, tmin, o));
+                    acc.x += __shfl_xor_sync(FULL, acc.x, o);
+                    acc.y += __shfl_xor_sync(FULL, acc.y, o);
+                    acc.z += __shfl_xor_sync(FULL, acc.z, o);
+                    acc.w += __shfl_xor_sync(FULL, acc.w, o);
+                    wsum += __shfl_xor_sync(FULL, wsum, o);
                 }
             }
-            // Smart order: FP32 decision outside the guard band, FP64 re-check inside it.
-            // The group leader does the re-check; every lane then takes part in the
-            // broadcast (a full-mask shuffle must be reached by all 32 lanes).
             // Smart order: decided in FP32 outside a guard band around c, re-checked in
             // FP64 inside it.  Band: relative 1e-4 for the rotated ball, where the FP32
             // error of both sums is below ~1e-5 relative (the m = 0 terms are exact and
@@ -522,9 +593,10 @@ __device__ void process_tile(const FillParams &p, const FrameDev &F, WarpSmem<RW
                 ready = d > tol;
                 recheck = !(d > tol) && !(d < -tol);
             }
-            if (act && j == 0 && (ready || recheck)) {
+            if (act && j == 0 && cnt > 0 && (ready || recheck)) {
                 atomicOr(recheck ? &ws->recheck : &ws->ready, 1ull << pix);
-                ws->rot[pix] = make_float4(ch, sh, beta, tmin);
+                const float inv = 1.0f / wsum;
+                ws->colr[pix] = make_float4(acc.x * inv, acc.y * inv, acc.z * inv, acc.w * inv);
             }
         }
     }
@@ -536,13 +608,22 @@ __device__ void process_tile(const FillParams &p, const FrameDev &F, WarpSmem<RW
         if (lane == 0 && r64) atomicOr(&ws->ready, 1ull << pix);
         wc.rechecks++;
     }
-    cp_async_wait_all();
     __syncwarp();
     const unsigned long long Rm = ws->ready;
     const int nr = __popcll(Rm);
 
-    // ---- tile bookkeeping and neighbour claims, issued before the colour pass so
-    //      that their round trips overlap it
+    // ---- the fills (state word k: not readable by any other test of step k)
+#pragma unroll
+    for (int h = 0; h < 2; h++) {
+        const int pix = lane + 32 * h;
+        if ((Rm >> pix) & 1ull) {
+            const size_t o = (size_t)(y0 + (pix >> 3)) * W + x0 + (pix & 7);
+            F.rgba[o] = ws->colr[pix];
+            F.shell[o] = k;
+        }
+    }
+
+    // ---- tile bookkeeping
     const unsigned long long Qnew = (Qold & ~cand) | (P & ~Rm);
     if (lane == 0) {
         if (Rm) {
@@ -555,13 +636,11 @@ __device__ void process_tile(const FillParams &p, const FrameDev &F, WarpSmem<RW
     }
     wc.filled += nr;
     wc.delta += __popcll(Qnew) - __popcll(Qold);
-    // Tiles for step k+1: the neighbours within reach of this step's fills.  Which
-    // neighbours to claim is known before any atomic, so the list slots are reserved
-    // while the claims (atomicMax on the tile's step word) are in flight; a claim
-    // lost to another tile leaves a skip marker (-1) in its slot.
-    bool need = false;
-    int nt = 0, basei = 0, oldsched = 0;
-    unsigned bm = 0u;
+
+    // ---- tiles for step k+1: the neighbours within reach of this step's fills
+    //      that still hold unfilled pixels.  The list slots are reserved with one
+    //      atomicAdd while the claims (atomicMax on the tile's step word) are in
+    //      flight; a claim lost to another tile leaves a skip marker (-1).
     if (MODE != RESCAN && Rm) {
         const int reach = R + 1;
         uint32_t colocc = 0, rowocc = 0;
@@ -574,120 +653,16 @@ __device__ void process_tile(const FillParams &p, const FrameDev &F, WarpSmem<RW
         const uint32_t lowm = reach >= 8 ? 0xffu : ((1u << reach) - 1u);
         const bool nL = (colocc & lowm) != 0, nR = (colocc >> (8 - (reach >= 8 ? 8 : reach))) != 0;
         const bool nU = (rowocc & lowm) != 0, nD = (rowocc >> (8 - (reach >= 8 ? 8 : reach))) != 0;
-        if (lane < 9) {
-            int dx = lane % 3 - 1, dy = lane / 3 - 1;
-            int nx = tx + dx, ny = ty + dy;
-            need = (dx == 0 || (dx < 0 ? nL : nR)) && (dy == 0 || (dy < 0 ? nU : nD)) && nx >= 0 && ny >= 0 &&
-                   nx < F.TW && ny < F.TH;
-            nt = ny * F.TW + nx;
-        }
-        bm = __ballot_sync(FULL, need);
+        const unsigned long long left = (lane == 4) ? (U & ~Rm) : unb;
+        const bool need = nvalid && (ndx == 0 || (ndx < 0 ? nL : nR)) && (ndy == 0 || (ndy < 0 ? nU : nD)) &&
+                          left != 0ull;
+        const unsigned bm = __ballot_sync(FULL, need);
         if (bm) {
-            if (lane == 0) basei = atomicAdd(&ctl->list_count[(k + 1) % 3], __popc(bm));
-            if (need) oldsched = atomicMax(&F.sched[nt], k + 1);
-        }
-    }
-
-    // ---- fill the ready pixels: normalised weighted average of bilinear ghost values
-    if (nr) {
-        const int G = nr <= 4 ? 8 : (nr <= 8 ? 4 : (nr <= 16 ? 2 : 1));
-        const int per = 32 / G;
-        const int j = lane & (G - 1), grp = lane / G;
-        for (int base = 0; base < nr; base += per) {
-            const int q = base + grp;
-            const bool act = q < nr;
-            const int pix = act ? nth_bit64(Rm, q) : 0;
-            const int px = pix & 7, py = pix >> 3;
-            const int gxp = x0 + px, gyp = y0 + py;
-            float2 g = make_float2(0.f, 0.f);
-            if (act && MODE != STALL) g = ws->guide[pix];
-            const bool rot = ghost && MODE != STALL;
-            const float4 rt = act ? ws->rot[pix] : make_float4(1.f, 0.f, 0.f, 0.f);
-            const float ch = rt.x, sh = rt.y, beta = rt.z, tmin = rt.w;
-            float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
-            float wsum = 0.f;
-            if (act) {
-                for (int gi = 0; gi <= R; gi++) {
-                    const float tg = beta * (float)(gi * gi);
-                    const float eg = expf(-(tg - tmin));
-                    for (int s = p.tab.m_start[gi] + j; s < p.tab.m_start[gi + 1]; s += G) {
-                        const float nf = p.tab.n_f[s], mf = p.tab.m_f[s];
-                        float ox, oy;
-                        if (rot) {
-                            ox = __fsub_rn(__fmul_rn(nf, ch), __fmul_rn(mf, sh));
-                            oy = __fadd_rn(__fmul_rn(nf, sh), __fmul_rn(mf, ch));
-                            float r0 = rintf(ox);
-                            if (fabsf(__fsub_rn(ox, r0)) <= p.tau) ox = r0;
-                            r0 = rintf(oy);
-                            if (fabsf(__fsub_rn(oy, r0)) <= p.tau) oy = r0;
-                        } else {
-                            ox = nf;
-                            oy = mf;
-                        }
-                        const float flx = floorf(ox), fly = floorf(oy);
-                        const float frx = __fsub_rn(ox, flx), fry = __fsub_rn(oy, fly);
-                        const int ix = px + RW + (int)flx, iy = py + RW + (int)fly;
-                        const uint32_t need = frx > 0.0f ? 3u : 1u;
-                        bool ok = ((ws->rowmask[iy] >> ix) & need) == need;
-                        if (fry > 0.0f) ok = ok && (((ws->rowmask[iy + 1] >> ix) & need) == need);
-                        if (!ok) continue;
-                        float w;
-                        if (ghost || MODE == STALL) {
-                            w = eg * p.tab.invd[s];
-                        } else {
-                            float proj = -g.y * nf + g.x * mf;
-                            w = expf(-(p.coef32 * proj * proj - tmin)) * p.tab.invd[s];
-                        }
-                        const float4 *cb = &ws->col[iy * WS + ix];
-                        float4 v = cb[0];
-                        float l00 = (1.f - frx) * (1.f - fry);
-                        float4 val = make_float4(l00 * v.x, l00 * v.y, l00 * v.z, l00 * v.w);
-                        if (frx > 0.f) {
-                            float l = frx * (1.f - fry);
-                            float4 c1 = cb[1];
-                            val.x += l * c1.x; val.y += l * c1.y; val.z += l * c1.z; val.w += l * c1.w;
-                        }
-                        if (fry > 0.f) {
-                            float l = (1.f - frx) * fry;
-                            float4 c2 = cb[WS];
-                            val.x += l * c2.x; val.y += l * c2.y; val.z += l * c2.z; val.w += l * c2.w;
-                            if (frx > 0.f) {
-                                float l3 = frx * fry;
-                                float4 c3 = cb[WS + 1];
-                                val.x += l3 * c3.x; val.y += l3 * c3.y; val.z += l3 * c3.z; val.w += l3 * c3.w;
-                            }
-                        }
-                        acc.x += w * val.x; acc.y += w * val.y; acc.z += w * val.z; acc.w += w * val.w;
-                        wsum += w;
-                    }
-                }
-            }
-#pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                if (o < G) {
-                    acc.x += __shfl_xor_sync(FULL, acc.x, o);
-                    acc.y += __shfl_xor_sync(FULL, acc.y, o);
-                    acc.z += __shfl_xor_sync(FULL, acc.z, o);
-                    acc.w += __shfl_xor_sync(FULL, acc.w, o);
-                    wsum += __shfl_xor_sync(FULL, wsum, o);
-                }
-            }
-            if (act && j == 0) {
-                float inv = 1.0f / wsum;
-                F.rgba[(size_t)gyp * W + gxp] = make_float4(acc.x * inv, acc.y * inv, acc.z * inv, acc.w * inv);
-                F.shell[(size_t)gyp * W + gxp] = k;
-            }
-        }
-    }
-
-
-    // ---- list entries of the claims (their atomics have returned by now)
-    if (bm) {
-        basei = __shfl_sync(FULL, basei, 0);
-        if (need) {
-            const int pos = basei + __popc(bm & ((1u << lane) - 1u));
-            if (pos < p.list_cap) lists[(size_t)((k + 1) % 3) * p.list_cap + pos] = oldsched < k + 1 ? nt : -1;
-            else wc.err = 1;
+            pc.bm = bm;
+            pc.k = k;
+            pc.nt = nt;
+            if (lane == 0) pc.base = atomicAdd(&ctl->list_count[(k + 1) % 3], __popc(bm));
+            if (need) pc.old = atomicMax(&F.sched[nt], k + 1);
         }
     }
 }
@@ -726,7 +701,7 @@ __device__ __forceinline__ void flush_counters(GroupCtl *ctl, const WarpCounters
 // selects the tile mask that makes a tile a member (U: rescan, Qw: stall).
 template <int RW, int MODE>
 __device__ void sweep_tiles(const FillParams &p, const FrameDev &F, WarpSmem<RW> *ws, GroupCtl *ctl,
-                            int32_t *lists, int k, int gw, int nw, WarpCounters &wc)
+                            int32_t *lists, int k, int gw, int nw, WarpCounters &wc, PendingClaims &pc)
 {
     const int lane = threadIdx.x & 31;
     for (int base = gw * 32; base < F.ntiles; base += nw * 32) {
@@ -738,7 +713,7 @@ __device__ void sweep_tiles(const FillParams &p, const FrameDev &F, WarpSmem<RW>
             int i = __ffs(bal) - 1;
             bal &= bal - 1;
             unsigned long long mi = __shfl_sync(FULL, m, i);
-            process_tile<RW, MODE>(p, F, ws, ctl, lists, base + i, k, mi, wc);
+            process_tile<RW, MODE>(p, F, ws, ctl, lists, base + i, k, mi, wc, pc);
         }
     }
 }
@@ -794,8 +769,10 @@ __global__ void __launch_bounds__(fill_warps(RW) * 32, 1) fill_kernel(const __gr
         for (;;) {
             const int slot = k % 3;
             WarpCounters wc = {0, 0, 0, 0, 0};
+            PendingClaims pc;
+            pc.bm = 0u;
             if (rescan) {
-                sweep_tiles<RW, RESCAN>(p, F, ws, ctl, lists, k, gw, nw, wc);
+                sweep_tiles<RW, RESCAN>(p, F, ws, ctl, lists, k, gw, nw, wc, pc);
             } else {
                 // step 0 takes the init kernel's list, later steps the lists built by the claims
                 const int n = n_cur;
@@ -809,17 +786,18 @@ __global__ void __launch_bounds__(fill_warps(RW) * 32, 1) fill_kernel(const __gr
                 int pre = 0;
                 if (lane0 && more) pre = atomicAdd(&ctl->cursor[slot], 1);
                 const int t0 = gw < n ? t0_cur : -1;
-                if (t0 >= 0) process_tile<RW, NORMAL>(p, F, ws, ctl, lists, t0, k, 0ull, wc);
+                if (t0 >= 0) process_tile<RW, NORMAL>(p, F, ws, ctl, lists, t0, k, 0ull, wc, pc);
                 if (more) {
                     int nxt = nw + __shfl_sync(FULL, pre, 0);
                     while (nxt < n) {
                         const int t = __ldcg(&L[nxt]);
                         if (lane0) pre = atomicAdd(&ctl->cursor[slot], 1);
-                        if (t >= 0) process_tile<RW, NORMAL>(p, F, ws, ctl, lists, t, k, 0ull, wc);
+                        if (t >= 0) process_tile<RW, NORMAL>(p, F, ws, ctl, lists, t, k, 0ull, wc, pc);
                         nxt = nw + __shfl_sync(FULL, pre, 0);
                     }
                 }
             }
+            write_claims(p, lists, pc, wc);
             flush_counters(ctl, wc, k, false, threadIdx.x < 32);
             cluster.sync();
             // one round trip: this step's counters and the next step's list
@@ -845,7 +823,8 @@ __global__ void __launch_bounds__(fill_warps(RW) * 32, 1) fill_kernel(const __gr
                 // stall pass adds to the same slot (its counters were zero after the
                 // evaluation pass, except the front delta).
                 WarpCounters ws2 = {0, 0, 0, 0, 0};
-                sweep_tiles<RW, STALL>(p, F, ws, ctl, lists, k, gw, nw, ws2);
+                sweep_tiles<RW, STALL>(p, F, ws, ctl, lists, k, gw, nw, ws2, pc);
+                write_claims(p, lists, pc, ws2);
                 flush_counters(ctl, ws2, k, true, false);
                 cluster.sync();
                 const int sf = __ldcg(&ctl->filled[slot]);
@@ -891,6 +870,7 @@ __global__ void __launch_bounds__(fill_warps(RW) * 32, 1) fill_kernel(const __gr
         }
         __syncthreads();
     }
+    cp_async_wait_all();  // window copies of a last tile that had no candidates
 }
 
 const void *fill_kernel_entry(int rw)

@@ -51,7 +51,7 @@ struct WarpSmem {
     float4 col[WS * WS];         // colour window (cp.async)
     float2 guide[64];            // guide vectors of the tile's candidate pixels
     uint32_t rowmask[WS];        // readable bits of the window rows
-    float4 rot[64];              // per ready pixel: unit guide (c, s), weight scale beta, smallest readable exponent
+    float4 colr[64];             // fill value of each ready (or re-checked) pixel
     unsigned long long ready;
     unsigned long long recheck;   // pixels whose ready test is re-done in FP64
 };

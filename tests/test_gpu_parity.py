@@ -78,7 +78,9 @@ def test_rescan_equals_tracking_and_counts_every_front_pixel():
     b = gpu_fill(d["rgb"], d["labels"], d["guide"], rescan=True)
     o = oracle_fill(d["rgb"], d["labels"], d["guide"])
     assert np.array_equal(a["shell"], b["shell"]) and np.array_equal(a["enter"], b["enter"])
-    assert np.array_equal(a["u"], b["u"])  # same FP32 operations in the same order
+    # Same fills; the colours agree to FP32 rounding (the lanes that share a pixel's
+    # samples follow the tile's front-pixel count, which a rescan sees larger).
+    assert np.nanmax(np.abs(a["u"] - b["u"])) <= 2e-6
     assert b["stats"]["evaluations"] == o["stats"]["evaluations"]  # rescan evaluates the whole front every step
     assert a["stats"]["evaluations"] < b["stats"]["evaluations"]
 
