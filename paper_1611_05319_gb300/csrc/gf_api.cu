@@ -124,6 +124,7 @@ void gf::build_tab(float eps, SampleTab &tab)
             }
         }
     tab.ns = (int)cn.size();
+    tab.nsp = (tab.ns + 31) / 32 * 32;  // padding entries stay (0, 0) with 1/|.| = 0 (memset above)
     tab.R = R;
     for (int s = 0; s < tab.ns; s++) {
         tab.cn[s] = (int8_t)cn[s];

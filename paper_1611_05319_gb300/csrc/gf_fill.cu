@@ -394,8 +394,6 @@ __device__ void process_tile(const FillParams &p, const FrameDev &F, WarpSmem<RW
         int gx = wx0 + c, gy = wy0 + r;
         if (gx >= 0 && gy >= 0 && gx < W && gy < H) cp_async16(&ws->col[e], &F.rgba[(size_t)gy * W + gx]);
     }
-    // the previous tile's claims have returned by now
-    write_claims(p, lists, pc, wc);
 
     unsigned long long cand;
     if (MODE == NORMAL) {
@@ -470,8 +468,10 @@ __device__ void process_tile(const FillParams &p, const FrameDev &F, WarpSmem<RW
         const int per = 32 / G;
         const int j = lane & (G - 1), grp = lane / G;
         const int ns = p.tab.ns;
+        const int nsp = p.tab.nsp;
         const bool rot = ghost && MODE != STALL;
         const bool iso = ghost || MODE == STALL;  // the exponent depends on |m| only
+        const bool fast = MODE == STALL || (ghost && smart && p.c >= 1e-30f);
         for (int base = 0; base < np; base += per) {
             const int q = base + grp;
             const bool act = q < np;
@@ -494,7 +494,56 @@ __device__ void process_tile(const FillParams &p, const FrameDev &F, WarpSmem<RW
             float S_rd = 0.f, S_all = 0.f, tmin = INFINITY, wsum = 0.f;
             float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
             int cnt = 0;
-            if (act) {
+            if (act && fast) {
+                // Rotated ball under smart order, or the stall pass: the weights need no
+                // normalisation (a ready pixel has S_rd > c S_all >= c times the m = 0
+                // weights; stall weights are 1/|(n, m)|).  Branch-free, two samples per
+                // round; taps of zero weight are selected away, never multiplied (an
+                // unreadable pixel's colour may be anything).
+                for (int s0 = j; s0 < nsp; s0 += 2 * G) {
+#pragma unroll
+                    for (int u = 0; u < 2; u++) {
+                        const int s = s0 + u * G;
+                        const float nf = p.tab.n_f[s], mf = p.tab.m_f[s], invd = p.tab.invd[s];
+                        float ox, oy;
+                        if (rot) {
+                            ox = __fsub_rn(__fmul_rn(nf, ch), __fmul_rn(mf, sh));
+                            oy = __fadd_rn(__fmul_rn(nf, sh), __fmul_rn(mf, ch));
+                            float r0 = rintf(ox);
+                            if (fabsf(__fsub_rn(ox, r0)) <= p.tau) ox = r0;
+                            r0 = rintf(oy);
+                            if (fabsf(__fsub_rn(oy, r0)) <= p.tau) oy = r0;
+                        } else {
+                            ox = nf;
+                            oy = mf;
+                        }
+                        const float flx = floorf(ox), fly = floorf(oy);
+                        const float frx = __fsub_rn(ox, flx), fry = __fsub_rn(oy, fly);
+                        const int ix = px + RW + (int)flx, iy = py + RW + (int)fly;
+                        const uint32_t need = frx > 0.0f ? 3u : 1u;
+                        const uint32_t rm0 = ws->rowmask[iy], rm1 = ws->rowmask[iy + 1];
+                        const bool ok = (((rm0 >> ix) & need) == need) && (!(fry > 0.0f) || (((rm1 >> ix) & need) == need));
+                        const float w0 = expf(-(beta * (mf * mf))) * invd;
+                        S_all += w0;
+                        const float4 *cb = &ws->col[iy * WS + ix];
+                        const float4 v = cb[0], c1 = cb[1], c2 = cb[WS], c3 = cb[WS + 1];
+                        const float l00 = (1.f - frx) * (1.f - fry);
+                        const float l10 = frx * (1.f - fry), l01 = (1.f - frx) * fry, l11 = frx * fry;
+                        const bool hx = frx > 0.f, hy = fry > 0.f, hxy = hx && hy;
+                        float4 val = make_float4(l00 * v.x, l00 * v.y, l00 * v.z, l00 * v.w);
+                        val.x += hx ? l10 * c1.x : 0.f; val.y += hx ? l10 * c1.y : 0.f;
+                        val.z += hx ? l10 * c1.z : 0.f; val.w += hx ? l10 * c1.w : 0.f;
+                        val.x += hy ? l01 * c2.x : 0.f; val.y += hy ? l01 * c2.y : 0.f;
+                        val.z += hy ? l01 * c2.z : 0.f; val.w += hy ? l01 * c2.w : 0.f;
+                        val.x += hxy ? l11 * c3.x : 0.f; val.y += hxy ? l11 * c3.y : 0.f;
+                        val.z += hxy ? l11 * c3.z : 0.f; val.w += hxy ? l11 * c3.w : 0.f;
+                        S_rd += ok ? w0 : 0.f;
+                        cnt += ok ? 1 : 0;
+                        acc.x += ok ? w0 * val.x : 0.f; acc.y += ok ? w0 * val.y : 0.f;
+                        acc.z += ok ? w0 * val.z : 0.f; acc.w += ok ? w0 * val.w : 0.f;
+                    }
+                }
+            } else if (act) {
 #pragma unroll 2
                 for (int s = j; s < ns; s += G) {
                     const float nf = p.tab.n_f[s], mf = p.tab.m_f[s], invd = p.tab.invd[s];
@@ -560,13 +609,17 @@ __device__ void process_tile(const FillParams &p, const FrameDev &F, WarpSmem<RW
                 }
             }
             // combine the G lanes of a pixel
-            float tg = tmin;
+            if (!fast) {
+                float tg = tmin;
 #pragma unroll
-            for (int o = 1; o < 32; o <<= 1)
-                if (o < G) tg = fminf(tg, __shfl_xor_sync(FULL, tg, o));
-            const float sc = (tmin == INFINITY) ? 0.f : expf(tg - tmin);
-            acc.x *= sc; acc.y *= sc; acc.z *= sc; acc.w *= sc;
-            wsum *= sc;
+                for (int o = 1; o < 32; o <<= 1)
+                    if (o < G) tg = fminf(tg, __shfl_xor_sync(FULL, tg, o));
+                const float sc = (tmin == INFINITY) ? 0.f : expf(tg - tmin);
+                acc.x *= sc; acc.y *= sc; acc.z *= sc; acc.w *= sc;
+                wsum *= sc;
+            } else {
+                wsum = S_rd;
+            }
 #pragma unroll
             for (int o = 1; o < 32; o <<= 1) {
                 if (o < G) {
@@ -636,6 +689,9 @@ __device__ void process_tile(const FillParams &p, const FrameDev &F, WarpSmem<RW
     }
     wc.filled += nr;
     wc.delta += __popcll(Qnew) - __popcll(Qold);
+
+    // the previous tile's claims have returned by now
+    write_claims(p, lists, pc, wc);
 
     // ---- tiles for step k+1: the neighbours within reach of this step's fills
     //      that still hold unfilled pixels.  The list slots are reserved with one

@@ -33,6 +33,7 @@ __host__ __device__ inline bool readable_at(int32_t s, int32_t k) {
 // the FP64 re-check walks them in canonical order (m ascending, n ascending).
 struct SampleTab {
     int ns;                      // number of samples
+    int nsp;                     // ns rounded up to a multiple of 32; entries ns.. are (0, 0) with weight 0
     int R;                       // ceil(eps)
     int m_start[MAX_R + 2];      // group |m| = g occupies [m_start[g], m_start[g+1])
     float Dm[MAX_R + 1];         // sum of 1/|(n,m)| over group g
