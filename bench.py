@@ -39,6 +39,29 @@ WORKLOAD = ("batched: 64 frames 1920x1080 RGBA fp32 (seeds 100-163), holes U[0.5
             "eps=3, mu=50, c=0.05, ghost ball, smart order, tracked front; in-place fill")
 SEED0, NFRAMES = 100, 64
 
+# DRAM traffic of fill_kernel per filled pixel from one ncu capture of the first 8
+# frames of this batch (dram__bytes_read.sum + dram__bytes_write.sum = 36.373504 MB +
+# 0.758784 MB for 534,164 filled pixels; profiles/fill_kernel_batch_8x1080.md).  It
+# holds only for the kernel sources it was taken on: with any other source the
+# roofline's traffic is reported as null.
+FILL_TRAFFIC = {
+    "sources": {
+        "paper_1611_05319_gb300/csrc/gf_fill.cu": "79b12a18d1f01057e6450256d7996e00e56c590e1496349c9c6e7e44c2748bc8",
+        "paper_1611_05319_gb300/csrc/gf_internal.cuh": "4ea9308c7bcf24250d5036e22588937919faf72d7edb3120393bdf8805cebbac",
+    },
+    "bytes_per_filled_px": (36.373504e6 + 0.758784e6) / 534164,
+}
+
+
+def fill_traffic(filled_px):
+    """Scaled DRAM bytes of one fill launch, or None if the kernel changed since the capture."""
+    import hashlib
+    for rel, digest in FILL_TRAFFIC["sources"].items():
+        with open(os.path.join(ROOT, rel), "rb") as fh:
+            if hashlib.sha256(fh.read()).hexdigest() != digest:
+                return None
+    return FILL_TRAFFIC["bytes_per_filled_px"] * filled_px
+
 
 def parse():
     p = argparse.ArgumentParser()
@@ -298,9 +321,11 @@ def main():
         alg, peak, src = None, 6800.0, "fallback"
     if alg is not None:
         ach = alg / (fill_ms / 1e3) / 1e9
-        roof = {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak, "traffic": None,
-                "kernel": "fill_kernel", "alg_bytes_per_launch": alg, "fill_kernel_ms": fill_ms,
-                "peak_source": src}
+        filled_launch = sum(gold[str(SEED0 + i)]["filled"] for i in range(n))
+        roof = {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
+                "traffic": fill_traffic(filled_launch), "kernel": "fill_kernel", "alg_bytes_per_launch": alg,
+                "fill_kernel_ms": fill_ms, "peak_source": src,
+                "traffic_note": "DRAM bytes per launch scaled by filled pixels from an ncu capture of 8 of the frames"}
 
     # ---- end to end through the host-buffer C-ABI call
     e2e = None
