@@ -41,6 +41,12 @@ namespace gf {
 
 constexpr unsigned FULL = 0xffffffffu;
 
+// The sample table of the fill kernel in shared memory: (n, m, 1/|(n, m)|, |m|)
+// in grouped order, padded to a multiple of 32 (one 16-byte load per sample; the
+// lanes of a pixel read different entries, which the constant cache would
+// serialise).
+__shared__ float4 g_stab[MAX_SAMPLES];
+
 // ---------------------------------------------------------------------------
 // init
 // ---------------------------------------------------------------------------
@@ -494,17 +500,27 @@ __device__ void process_tile(const FillParams &p, const FrameDev &F, WarpSmem<RW
             float S_rd = 0.f, S_all = 0.f, tmin = INFINITY, wsum = 0.f;
             float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
             int cnt = 0;
+            if (fast) {
+                // group weights e^(-beta g^2), g = |m| = 0..R, shared by the pixel's G lanes
+                __syncwarp();
+                if (act)
+                    for (int gg = j; gg <= R; gg += G) ws->eg[grp][gg] = expf(-(beta * (float)(gg * gg)));
+                __syncwarp();
+            }
             if (act && fast) {
                 // Rotated ball under smart order, or the stall pass: the weights need no
                 // normalisation (a ready pixel has S_rd > c S_all >= c times the m = 0
                 // weights; stall weights are 1/|(n, m)|).  Branch-free, two samples per
-                // round; taps of zero weight are selected away, never multiplied (an
-                // unreadable pixel's colour may be anything).
+                // round.  Taps of zero weight and the taps of unreadable samples are read
+                // from the window's zero entry (an unreadable pixel's colour may be
+                // anything, and 0 * NaN is NaN).
+                constexpr int ZI = WS * WS;
+                const float *eg = ws->eg[grp];
                 for (int s0 = j; s0 < nsp; s0 += 2 * G) {
 #pragma unroll
                     for (int u = 0; u < 2; u++) {
-                        const int s = s0 + u * G;
-                        const float nf = p.tab.n_f[s], mf = p.tab.m_f[s], invd = p.tab.invd[s];
+                        const float4 te = g_stab[s0 + u * G];  // n, m, 1/|(n, m)|, |m|
+                        const float nf = te.x, mf = te.y, invd = te.z;
                         float ox, oy;
                         if (rot) {
                             ox = __fsub_rn(__fmul_rn(nf, ch), __fmul_rn(mf, sh));
@@ -520,33 +536,36 @@ __device__ void process_tile(const FillParams &p, const FrameDev &F, WarpSmem<RW
                         const float flx = floorf(ox), fly = floorf(oy);
                         const float frx = __fsub_rn(ox, flx), fry = __fsub_rn(oy, fly);
                         const int ix = px + RW + (int)flx, iy = py + RW + (int)fly;
-                        const uint32_t need = frx > 0.0f ? 3u : 1u;
+                        const bool hx = frx > 0.0f, hy = fry > 0.0f;
+                        const uint32_t need = hx ? 3u : 1u;
                         const uint32_t rm0 = ws->rowmask[iy], rm1 = ws->rowmask[iy + 1];
-                        const bool ok = (((rm0 >> ix) & need) == need) && (!(fry > 0.0f) || (((rm1 >> ix) & need) == need));
-                        const float w0 = expf(-(beta * (mf * mf))) * invd;
+                        const bool ok = (((rm0 >> ix) & need) == need) && (!hy || (((rm1 >> ix) & need) == need));
+                        const float w0 = eg[(int)te.w] * invd;
                         S_all += w0;
-                        const float4 *cb = &ws->col[iy * WS + ix];
-                        const float4 v = cb[0], c1 = cb[1], c2 = cb[WS], c3 = cb[WS + 1];
-                        const float l00 = (1.f - frx) * (1.f - fry);
-                        const float l10 = frx * (1.f - fry), l01 = (1.f - frx) * fry, l11 = frx * fry;
-                        const bool hx = frx > 0.f, hy = fry > 0.f, hxy = hx && hy;
-                        float4 val = make_float4(l00 * v.x, l00 * v.y, l00 * v.z, l00 * v.w);
-                        val.x += hx ? l10 * c1.x : 0.f; val.y += hx ? l10 * c1.y : 0.f;
-                        val.z += hx ? l10 * c1.z : 0.f; val.w += hx ? l10 * c1.w : 0.f;
-                        val.x += hy ? l01 * c2.x : 0.f; val.y += hy ? l01 * c2.y : 0.f;
-                        val.z += hy ? l01 * c2.z : 0.f; val.w += hy ? l01 * c2.w : 0.f;
-                        val.x += hxy ? l11 * c3.x : 0.f; val.y += hxy ? l11 * c3.y : 0.f;
-                        val.z += hxy ? l11 * c3.z : 0.f; val.w += hxy ? l11 * c3.w : 0.f;
                         S_rd += ok ? w0 : 0.f;
                         cnt += ok ? 1 : 0;
-                        acc.x += ok ? w0 * val.x : 0.f; acc.y += ok ? w0 * val.y : 0.f;
-                        acc.z += ok ? w0 * val.z : 0.f; acc.w += ok ? w0 * val.w : 0.f;
+                        const int b0 = iy * WS + ix;
+                        const float4 v = ws->col[ok ? b0 : ZI];
+                        const float4 c1 = ws->col[ok && hx ? b0 + 1 : ZI];
+                        const float4 c2 = ws->col[ok && hy ? b0 + WS : ZI];
+                        const float4 c3 = ws->col[ok && hx && hy ? b0 + WS + 1 : ZI];
+                        const float gx = 1.f - frx, gy = 1.f - fry;
+                        const float l00 = gx * gy, l10 = frx * gy, l01 = gx * fry, l11 = frx * fry;
+                        const float vx = __fmaf_rn(l11, c3.x, __fmaf_rn(l01, c2.x, __fmaf_rn(l10, c1.x, l00 * v.x)));
+                        const float vy = __fmaf_rn(l11, c3.y, __fmaf_rn(l01, c2.y, __fmaf_rn(l10, c1.y, l00 * v.y)));
+                        const float vz = __fmaf_rn(l11, c3.z, __fmaf_rn(l01, c2.z, __fmaf_rn(l10, c1.z, l00 * v.z)));
+                        const float vw = __fmaf_rn(l11, c3.w, __fmaf_rn(l01, c2.w, __fmaf_rn(l10, c1.w, l00 * v.w)));
+                        acc.x = __fmaf_rn(w0, vx, acc.x);
+                        acc.y = __fmaf_rn(w0, vy, acc.y);
+                        acc.z = __fmaf_rn(w0, vz, acc.z);
+                        acc.w = __fmaf_rn(w0, vw, acc.w);
                     }
                 }
             } else if (act) {
 #pragma unroll 2
                 for (int s = j; s < ns; s += G) {
-                    const float nf = p.tab.n_f[s], mf = p.tab.m_f[s], invd = p.tab.invd[s];
+                    const float4 te = g_stab[s];
+                    const float nf = te.x, mf = te.y, invd = te.z;
                     float ox, oy;
                     if (rot) {
                         ox = __fsub_rn(__fmul_rn(nf, ch), __fmul_rn(mf, sh));
@@ -790,6 +809,10 @@ __global__ void __launch_bounds__(fill_warps(RW) * 32, 1) fill_kernel(const __gr
     const int nw = csize * fill_warps(RW);
     const bool leader = crank == 0 && threadIdx.x == 0;
     const bool rescan = (p.flags & GF_FLAG_RESCAN) != 0;
+    for (int i = threadIdx.x; i < p.tab.nsp; i += blockDim.x)
+        g_stab[i] = make_float4(p.tab.n_f[i], p.tab.m_f[i], p.tab.invd[i], fabsf(p.tab.m_f[i]));
+    if ((threadIdx.x & 31) == 0) ws->col[WarpSmem<RW>::WS * WarpSmem<RW>::WS] = make_float4(0.f, 0.f, 0.f, 0.f);
+    __syncthreads();
 
     for (int it = 0;; it++) {
         cluster.sync();  // everyone is done with the previous frame's counters

@@ -49,10 +49,11 @@ struct SampleTab {
 template <int RW>
 struct WarpSmem {
     static constexpr int WS = TILE + 2 * RW;
-    float4 col[WS * WS];         // colour window (cp.async)
+    float4 col[WS * WS + 1];     // colour window (cp.async); the extra last entry stays zero
     float2 guide[64];            // guide vectors of the tile's candidate pixels
     uint32_t rowmask[WS];        // readable bits of the window rows
     float4 colr[64];             // fill value of each ready (or re-checked) pixel
+    float eg[32][MAX_R + 1];     // per pixel slot of a pass: e^(-beta g^2) for g = |m| = 0..R
     unsigned long long ready;
     unsigned long long recheck;   // pixels whose ready test is re-done in FP64
 };
