@@ -314,29 +314,65 @@ struct WarpCounters {
     int filled, delta, evals, err, rechecks;
 };
 
-// Neighbour-tile claims made by a warp's last tile: the list slots are written
-// once their atomics have returned, i.e. after the warp has issued the loads of
-// its next tile (or before the step's counter flush).
+// Neighbour-tile claims of step k (tiles for the work list of step k+1).  A claim
+// is an atomicMax of k+1 on the tile's step word; the claim that raises it wins.
+// Two ways to turn claims into list entries:
+//  * combined: list slots for every claim are reserved together with the claims
+//    (one round trip); a lost claim leaves a skip marker (-1) in its slot;
+//  * deferred: the warp reserves slots only for the claims it won, once their
+//    atomics have returned (at its next tile), and writes the entries one tile
+//    later, so the list holds no skip markers.  Used when a step's list is longer
+//    than the cluster's warp count, where markers would be walked one by one.
+// The struct carries the claims of a warp's last tiles between those points.
 struct PendingClaims {
-    unsigned bm;  // lanes (< 9) holding a claim, 0 if none
-    int base;     // lane 0: first reserved list slot
-    int old;      // per lane: the claimed tile's previous step word
-    int nt;       // per lane: the claimed tile
-    int k;        // step the claims were made at
+    unsigned m1;  // claims made, slots not yet reserved (warp-uniform lane mask)
+    unsigned m2;  // slots reserved, entries not yet written (warp-uniform lane mask)
+    int nt1, old1;  // per lane: claimed tile, previous step word
+    int nt2, old2;  // per lane: entry tile; old2 >= k+1 turns it into a skip marker
+    int base2;      // lane 0: first reserved slot
+    int k;          // step of the pending claims
 };
 
-__device__ __forceinline__ void write_claims(const FillParams &p, int32_t *lists, PendingClaims &pc, WarpCounters &wc)
+// Writes the reserved entries (their slot reservation has returned).
+__device__ __forceinline__ void claims_write(const FillParams &p, int32_t *lists, PendingClaims &pc, WarpCounters &wc)
 {
-    if (pc.bm) {  // warp-uniform
+    if (pc.m2) {  // warp-uniform
         const int lane = threadIdx.x & 31;
-        const int base = __shfl_sync(FULL, pc.base, 0);
-        if ((pc.bm >> lane) & 1u) {
-            const int pos = base + __popc(pc.bm & ((1u << lane) - 1u));
-            if (pos < p.list_cap) lists[(size_t)((pc.k + 1) % 3) * p.list_cap + pos] = pc.old < pc.k + 1 ? pc.nt : -1;
+        const int base = __shfl_sync(FULL, pc.base2, 0);
+        if ((pc.m2 >> lane) & 1u) {
+            const int pos = base + __popc(pc.m2 & ((1u << lane) - 1u));
+            if (pos < p.list_cap) lists[(size_t)((pc.k + 1) % 3) * p.list_cap + pos] = pc.old2 < pc.k + 1 ? pc.nt2 : -1;
             else wc.err = 1;
         }
-        pc.bm = 0u;
+        pc.m2 = 0u;
     }
+}
+
+// Reserves slots for the won claims among the deferred ones (their claims have
+// returned).  Stage 2 must be empty.
+__device__ __forceinline__ void claims_reserve(GroupCtl *ctl, PendingClaims &pc)
+{
+    if (pc.m1) {  // warp-uniform
+        const int lane = threadIdx.x & 31;
+        const bool won = ((pc.m1 >> lane) & 1u) && pc.old1 < pc.k + 1;
+        const unsigned wb = __ballot_sync(FULL, won);
+        if (wb) {
+            if (lane == 0) pc.base2 = atomicAdd(&ctl->list_count[(pc.k + 1) % 3], __popc(wb));
+            pc.nt2 = pc.nt1;
+            pc.old2 = INT32_MIN;
+            pc.m2 = wb;
+        }
+        pc.m1 = 0u;
+    }
+}
+
+// Everything pending is written (before the step's counter flush).
+__device__ __forceinline__ void claims_drain(const FillParams &p, GroupCtl *ctl, int32_t *lists, PendingClaims &pc,
+                                             WarpCounters &wc)
+{
+    claims_write(p, lists, pc, wc);
+    claims_reserve(ctl, pc);
+    claims_write(p, lists, pc, wc);
 }
 
 // Processes one tile at step k (one warp): candidates, exact front test, ready
@@ -345,7 +381,7 @@ __device__ __forceinline__ void write_claims(const FillParams &p, int32_t *lists
 template <int RW, int MODE>
 __device__ void process_tile(const FillParams &p, const FrameDev &F, WarpSmem<RW> *ws, GroupCtl *ctl,
                              int32_t *lists, int t, int k, unsigned long long cand_in, WarpCounters &wc,
-                             PendingClaims &pc)
+                             PendingClaims &pc, bool defer)
 {
     constexpr int WS = WarpSmem<RW>::WS;
     const int lane = threadIdx.x & 31;
@@ -709,8 +745,9 @@ __device__ void process_tile(const FillParams &p, const FrameDev &F, WarpSmem<RW
     wc.filled += nr;
     wc.delta += __popcll(Qnew) - __popcll(Qold);
 
-    // the previous tile's claims have returned by now
-    write_claims(p, lists, pc, wc);
+    // the previous tiles' claims and reservations have returned by now
+    claims_write(p, lists, pc, wc);
+    claims_reserve(ctl, pc);
 
     // ---- tiles for step k+1: the neighbours within reach of this step's fills
     //      that still hold unfilled pixels.  The list slots are reserved with one
@@ -733,11 +770,17 @@ __device__ void process_tile(const FillParams &p, const FrameDev &F, WarpSmem<RW
                           left != 0ull;
         const unsigned bm = __ballot_sync(FULL, need);
         if (bm) {
-            pc.bm = bm;
             pc.k = k;
-            pc.nt = nt;
-            if (lane == 0) pc.base = atomicAdd(&ctl->list_count[(k + 1) % 3], __popc(bm));
-            if (need) pc.old = atomicMax(&F.sched[nt], k + 1);
+            if (defer) {
+                pc.m1 = bm;
+                pc.nt1 = nt;
+                if (need) pc.old1 = atomicMax(&F.sched[nt], k + 1);
+            } else {
+                pc.m2 = bm;
+                pc.nt2 = nt;
+                if (lane == 0) pc.base2 = atomicAdd(&ctl->list_count[(k + 1) % 3], __popc(bm));
+                if (need) pc.old2 = atomicMax(&F.sched[nt], k + 1);
+            }
         }
     }
 }
@@ -788,7 +831,7 @@ __device__ void sweep_tiles(const FillParams &p, const FrameDev &F, WarpSmem<RW>
             int i = __ffs(bal) - 1;
             bal &= bal - 1;
             unsigned long long mi = __shfl_sync(FULL, m, i);
-            process_tile<RW, MODE>(p, F, ws, ctl, lists, base + i, k, mi, wc, pc);
+            process_tile<RW, MODE>(p, F, ws, ctl, lists, base + i, k, mi, wc, pc, false);
         }
     }
 }
@@ -849,7 +892,8 @@ __global__ void __launch_bounds__(fill_warps(RW) * 32, 1) fill_kernel(const __gr
             const int slot = k % 3;
             WarpCounters wc = {0, 0, 0, 0, 0};
             PendingClaims pc;
-            pc.bm = 0u;
+            pc.m1 = 0u;
+            pc.m2 = 0u;
             if (rescan) {
                 sweep_tiles<RW, RESCAN>(p, F, ws, ctl, lists, k, gw, nw, wc, pc);
             } else {
@@ -865,18 +909,18 @@ __global__ void __launch_bounds__(fill_warps(RW) * 32, 1) fill_kernel(const __gr
                 int pre = 0;
                 if (lane0 && more) pre = atomicAdd(&ctl->cursor[slot], 1);
                 const int t0 = gw < n ? t0_cur : -1;
-                if (t0 >= 0) process_tile<RW, NORMAL>(p, F, ws, ctl, lists, t0, k, 0ull, wc, pc);
+                if (t0 >= 0) process_tile<RW, NORMAL>(p, F, ws, ctl, lists, t0, k, 0ull, wc, pc, more);
                 if (more) {
                     int nxt = nw + __shfl_sync(FULL, pre, 0);
                     while (nxt < n) {
                         const int t = __ldcg(&L[nxt]);
                         if (lane0) pre = atomicAdd(&ctl->cursor[slot], 1);
-                        if (t >= 0) process_tile<RW, NORMAL>(p, F, ws, ctl, lists, t, k, 0ull, wc, pc);
+                        if (t >= 0) process_tile<RW, NORMAL>(p, F, ws, ctl, lists, t, k, 0ull, wc, pc, more);
                         nxt = nw + __shfl_sync(FULL, pre, 0);
                     }
                 }
             }
-            write_claims(p, lists, pc, wc);
+            claims_drain(p, ctl, lists, pc, wc);
             flush_counters(ctl, wc, k, false, threadIdx.x < 32);
             cluster.sync();
             // one round trip: this step's counters and the next step's list
@@ -903,7 +947,7 @@ __global__ void __launch_bounds__(fill_warps(RW) * 32, 1) fill_kernel(const __gr
                 // evaluation pass, except the front delta).
                 WarpCounters ws2 = {0, 0, 0, 0, 0};
                 sweep_tiles<RW, STALL>(p, F, ws, ctl, lists, k, gw, nw, ws2, pc);
-                write_claims(p, lists, pc, ws2);
+                claims_drain(p, ctl, lists, pc, ws2);
                 flush_counters(ctl, ws2, k, true, false);
                 cluster.sync();
                 const int sf = __ldcg(&ctl->filled[slot]);
