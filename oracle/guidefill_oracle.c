@@ -411,6 +411,7 @@ int oracle_guidance(int H, int W, const uint8_t *lab, int n_splines, const int32
     if (H <= 0 || W <= 0 || n_splines < 0 || !(eta > 0.0f)) return -1;
     float t3 = 3.0f * eta;
     float thr = t3 * t3;
+    double k2 = 1.0 / (2.0 * (double)eta * (double)eta); /* 1/(2 eta^2) */
     for (int y = 0; y < H; y++)
         for (int x = 0; x < W; x++) {
             size_t p = (size_t)y * W + x;
@@ -437,17 +438,21 @@ int oracle_guidance(int H, int W, const uint8_t *lab, int n_splines, const int32
                 guide[2 * p + 1] = 0.0f;
                 continue;
             }
+            /* FP64 value for the chosen segment: t = ((x - a).v) * (1/|v|^2) clamped to
+             * [0, 1], d^2 = |x - a - t v|^2, g = (v/|v|) * exp(-(d^2 * (1/(2 eta^2)))),
+             * rounded once to FP32 (Section 3.3). */
             double ax = pts[2 * bi], ay = pts[2 * bi + 1];
             double bx = pts[2 * bi + 2], by = pts[2 * bi + 3];
             double vx = bx - ax, vy = by - ay;
             double len = sqrt(vx * vx + vy * vy);
+            double inv_l2 = 1.0 / (len * len);
             double wx = (double)x - ax, wy = (double)y - ay;
-            double t = (wx * vx + wy * vy) / (len * len);
+            double t = (wx * vx + wy * vy) * inv_l2;
             if (t < 0.0) t = 0.0;
             if (t > 1.0) t = 1.0;
             double qx = wx - t * vx, qy = wy - t * vy;
             double d2 = qx * qx + qy * qy;
-            double e = exp(-d2 / (2.0 * (double)eta * (double)eta));
+            double e = exp(-(d2 * k2));
             guide[2 * p] = (float)(vx / len * e);
             guide[2 * p + 1] = (float)(vy / len * e);
         }
