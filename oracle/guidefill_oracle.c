@@ -393,9 +393,10 @@ static float seg_dist2_f32(float px, float py, float ax, float ay, float bx, flo
     float wx = px - ax, wy = py - ay;
     float l2 = vx * vx;
     l2 = l2 + vy * vy;
+    float inv_l2 = 1.0f / l2; /* once per segment in the CUDA sampler */
     float dot = wx * vx;
     dot = dot + wy * vy;
-    float t = dot / l2;
+    float t = dot * inv_l2;
     if (t < 0.0f) t = 0.0f;
     if (t > 1.0f) t = 1.0f;
     float qx = wx - t * vx;
