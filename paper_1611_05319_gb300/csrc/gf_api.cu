@@ -732,7 +732,9 @@ gf_status gf_guidance_batched(gf_ctx *ctx, int n, const gf_spline_frame *frames,
     ga.point_offset = (const int32_t *)(A + off_po);
     ga.bin_offset = (const int32_t *)(A + off_bo);
     ga.n_frames = n;
+    ga.total_bins = (int32_t)bb;
     ga.eta = eta;
+    ga.k2 = 1.0 / (2.0 * (double)eta * (double)eta);
     if (pp > 0) {
         bin_kernel<<<(unsigned)((pp + 255) / 256), 256, 0, st>>>(ga, (int)pp);
         CK(cudaGetLastError());

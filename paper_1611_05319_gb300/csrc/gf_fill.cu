@@ -54,7 +54,10 @@ __shared__ float4 g_stab[MAX_SAMPLES];
 
 __global__ void __launch_bounds__(256) init_kernel(const __grid_constant__ InitArgs a)
 {
-    __shared__ uint8_t lab_s[10][264];
+    // labels of rows y0-1 .. y0+8, columns x0-16 .. x0+271 (0xff outside the image);
+    // column x of the strip sits at index x - x0 + 16
+    __shared__ __align__(16) uint8_t lab_s[10][288];
+    __shared__ __align__(16) int32_t out_s[TILE][256];  // state words of the strip
     int b = blockIdx.x;
     int lo = 0, hi = a.n_frames;  // frame f with cta_offset[f] <= b < cta_offset[f+1]
     while (hi - lo > 1) {
@@ -69,14 +72,26 @@ __global__ void __launch_bounds__(256) init_kernel(const __grid_constant__ InitA
     const int x0 = (local - ty * strips) * 256;
     const int y0 = ty * TILE;
     const int t = threadIdx.x;
+    // 16-byte label loads and state-word stores when every row starts on a 16-byte boundary
+    const bool vec = (W & 15) == 0 && (reinterpret_cast<uintptr_t>(F.labels) & 15u) == 0 &&
+                     (reinterpret_cast<uintptr_t>(F.shell) & 15u) == 0;
 
-    // labels of rows y0-1 .. y0+8, columns x0-1 .. x0+256 (0xff outside the image)
-    for (int e = t; e < 10 * 258; e += 256) {
-        int r = e / 258, c = e - r * 258;
-        int y = y0 - 1 + r, x = x0 - 1 + c;
-        uint8_t v = 0xff;
-        if (y >= 0 && y < H && x >= 0 && x < W) v = __ldg(&F.labels[(size_t)y * W + x]);
-        lab_s[r][c] = v;
+    if (vec) {
+        for (int e = t; e < 10 * 18; e += 256) {
+            const int r = e / 18, c = e - r * 18;
+            const int y = y0 - 1 + r, x = x0 - 16 + 16 * c;
+            uint4 v = make_uint4(0xffffffffu, 0xffffffffu, 0xffffffffu, 0xffffffffu);
+            if (y >= 0 && y < H && x >= 0 && x < W) v = __ldg(reinterpret_cast<const uint4 *>(F.labels + (size_t)y * W + x));
+            *reinterpret_cast<uint4 *>(&lab_s[r][16 * c]) = v;
+        }
+    } else {
+        for (int e = t; e < 10 * 258; e += 256) {
+            const int r = e / 258, c = e - r * 258;
+            const int y = y0 - 1 + r, x = x0 - 1 + c;
+            uint8_t v = 0xff;
+            if (y >= 0 && y < H && x >= 0 && x < W) v = __ldg(&F.labels[(size_t)y * W + x]);
+            lab_s[r][c + 15] = v;
+        }
     }
     __syncthreads();
 
@@ -87,7 +102,7 @@ __global__ void __launch_bounds__(256) init_kernel(const __grid_constant__ InitA
     for (int r = 0; r < TILE; r++) {
         int y = y0 + r;
         bool in = (y < H) && (x < W);
-        uint8_t l = in ? lab_s[r + 1][t + 1] : 0xff;
+        uint8_t l = in ? lab_s[r + 1][t + 16] : 0xff;
         bool hole = in && l == 1;
         bool front = false;
         if (hole) {
@@ -95,19 +110,27 @@ __global__ void __launch_bounds__(256) init_kernel(const __grid_constant__ InitA
             for (int dy = 0; dy < 3; dy++)
 #pragma unroll
                 for (int dx = 0; dx < 3; dx++)
-                    if (!(dx == 1 && dy == 1) && lab_s[r + dy][t + dx] == 0) front = true;
+                    if (!(dx == 1 && dy == 1) && lab_s[r + dy][t + 15 + dx] == 0) front = true;
         }
-        if (in) {
-            int32_t s = (l == 0) ? SH_KNOWN : (l == 1 ? SH_UNFILLED : SH_BYST);
-            F.shell[(size_t)y * W + x] = s;
-            if (F.enter) F.enter[(size_t)y * W + x] = front ? 0 : -1;
-        }
+        const int32_t sw = (l == 0) ? SH_KNOWN : (l == 1 ? SH_UNFILLED : SH_BYST);
+        if (vec) out_s[r][t] = sw;
+        else if (in) F.shell[(size_t)y * W + x] = sw;
+        if (in && F.enter) F.enter[(size_t)y * W + x] = front ? 0 : -1;  // optional map, plain stores
         unsigned hb = __ballot_sync(FULL, hole);
         unsigned fb = __ballot_sync(FULL, front);
 #pragma unroll
         for (int q = 0; q < 4; q++) {
             Um[q] |= (unsigned long long)((hb >> (8 * q)) & 0xffu) << (8 * r);
             Qm[q] |= (unsigned long long)((fb >> (8 * q)) & 0xffu) << (8 * r);
+        }
+    }
+    if (vec) {
+        __syncthreads();
+        for (int e = t; e < TILE * 64; e += 256) {
+            const int r = e >> 6, c4 = e & 63;
+            const int y = y0 + r, x = x0 + 4 * c4;
+            if (y < H && x < W)
+                *reinterpret_cast<int4 *>(F.shell + (size_t)y * W + x) = *reinterpret_cast<const int4 *>(&out_s[r][4 * c4]);
         }
     }
     const int warp = t >> 5;

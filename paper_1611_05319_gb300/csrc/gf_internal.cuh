@@ -128,7 +128,7 @@ struct InitArgs {
 
 // guide-field sampler
 constexpr int BIN = 32;       // bins of 32x32 pixels
-constexpr int BIN_CAP = 64;   // segments listed per bin before falling back to a full scan
+constexpr int BIN_CAP = 256;  // segments listed per bin before falling back to a full scan
 
 struct SplineFrameDev {
     int32_t H, W, NBX, NBY;
@@ -139,7 +139,7 @@ struct SplineFrameDev {
     float2 *guide;
     int32_t *bin_count;  // [NBX*NBY]
     int32_t *bin_list;   // [NBX*NBY*BIN_CAP]
-    double *seg64;       // [n_points][8]: per segment start a, v = b - a, |v|^2 (as |v|*|v|), v/|v| (FP64)
+    double *seg64;       // [n_points][8]: per segment start a, v = b - a, 1/(|v|*|v|), v/|v| (FP64)
 };
 
 struct GuideArgs {
@@ -147,7 +147,9 @@ struct GuideArgs {
     const int32_t *point_offset;  // [n+1] first global point of each frame
     const int32_t *bin_offset;    // [n+1] first global bin of each frame
     int32_t n_frames;
+    int32_t total_bins;
     float eta;
+    double k2;                    // 1 / (2 eta^2) in FP64
 };
 
 constexpr int DESC_CHUNK = 128;  // frame descriptors per upload kernel
