@@ -350,11 +350,12 @@ def main():
         e2e = {"value": world * fe / w, "unit": "filled px/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                "ms_per_step": w * 1e3, "call": "gf_fill_batched_host (pinned host buffers, splines in)"}
 
-    extra4k = adjoint = single = None
+    extra4k = adjoint = single = complexity = None
     if rank == 0 and not args.no_extra:
         single = leg_1080(ctx, dev, stream, max(10, args.extra_steps))
         extra4k = leg_4k(ctx, dev, stream, args.extra_steps)
         adjoint = leg_adjoint(ctx, dev, stream, args.extra_steps)
+        complexity = leg_complexity(ctx, dev, stream, args.extra_steps)
 
     if rank != 0:
         if dist:
@@ -373,6 +374,7 @@ def main():
         "plain": plain, "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
         "gpu_launches": launches_per_step * K, "clocks": clocks,
         "single_1080": single, "tracked_vs_rescan_4k": extra4k, "adjoint_16x512": adjoint,
+        "complexity_line": complexity,
         "status_errors": bad,
     }
     print(json.dumps(line), flush=True)
@@ -489,6 +491,67 @@ def leg_4k(ctx, dev, stream, steps):
     out["speedup_tracked_over_rescan"] = out["rescan"]["fill_kernel_ms"] / out["tracked"]["fill_kernel_ms"]
     out["workload"] = "3840x2160, 400x400 blob + bands along 20 splines (seed 3), eps=4, mu=50, one frame"
     return out
+
+
+def leg_complexity(ctx, dev, stream, steps):
+    """Section 7's complexity validation on GB300: the line problem (a line
+    0.45 <= y <= 0.55 across D = [0.4, 3.96] x [0.2, 0.8] of [0, 4] x [0, 1],
+    smart order off, no splines) rendered from 280x70 to 4000x1000 px, filled
+    with the tracked front and with the full rescan; least-squares power laws
+    T(N) ~ A N^alpha of the fill-kernel time and P(N) ~ B N^beta of the pixels a
+    step hands to the GPU (the largest front with tracking, every hole pixel
+    without)."""
+    import ctypes as C
+
+    import numpy as np
+    import torch
+
+    from synth import configs, to_rgba
+    from paper_1611_05319_gb300 import _lib
+    L = _lib.lib()
+    sp = C.c_void_p(stream.cuda_stream)
+    rows = []
+    for H in (70, 140, 280, 500, 1000):
+        f = configs.line_problem(H)
+        W = 4 * H
+        lab = torch.from_numpy(f["labels"]).to(dev)
+        img = torch.from_numpy(to_rgba(f["rgb"])).to(dev)
+        g = torch.from_numpy(f["guide"]).to(dev)
+        shell = torch.empty((H, W), dtype=torch.int32, device=dev)
+        stats = torch.zeros((_lib.STATS_BYTES,), dtype=torch.uint8, device=dev)
+        fr = (_lib.Frame * 1)(_lib.Frame(H, W, img.data_ptr(), lab.data_ptr(), g.data_ptr(), img.data_ptr(),
+                                         shell.data_ptr(), None, None))
+        row = {"H": H, "W": W, "N": int((f["labels"] == 1).sum())}
+        for name, rescan in (("tracked", False), ("rescan", True)):
+            prm = _lib.make_params(eps=3.0, mu=50.0, c=0.05, smart=False, rescan=rescan)
+            evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+            for a, b in evs:
+                a.record(stream)
+                b.record(stream)
+            for k in range(steps + 1):
+                e = evs[k - 1] if k > 0 else None
+                _lib.check(L.gf_fill_batched_ex(ctx._h, 1, fr, C.byref(prm), C.c_void_p(stats.data_ptr()), sp,
+                                                C.c_void_p(e[0].cuda_event) if e else None,
+                                                C.c_void_p(e[1].cuda_event) if e else None), "fill", ctx._h)
+            torch.cuda.synchronize()
+            st = np.frombuffer(stats.cpu().numpy().tobytes(), dtype=_lib.STATS_DTYPE)[0]
+            row[name] = {"fill_kernel_ms": float(np.median([a.elapsed_time(b) for a, b in evs])),
+                         "shells": int(st["shells"]), "max_front": int(st["max_front"]),
+                         "launch": "cluster %d x %d" % ctx.last_launch()}
+        rows.append(row)
+    N = np.log([r["N"] for r in rows])
+
+    def fit(y):
+        return float(np.polyfit(N, np.log(y), 1)[0])
+    return {
+        "sizes": rows,
+        "alpha_tracked": fit([r["tracked"]["fill_kernel_ms"] for r in rows]),
+        "alpha_rescan": fit([r["rescan"]["fill_kernel_ms"] for r in rows]),
+        "beta_tracked": fit([r["tracked"]["max_front"] for r in rows]),
+        "beta_rescan": 1.0,
+        "paper": "alpha 0.54 / 1.10 and beta 0.5 / 1.0 with / without tracking on a GTX 970M",
+        "workload": "line problem of Section 7 at 280x70 ... 4000x1000 px, eps=3, smart order off, g = 0",
+    }
 
 
 def leg_adjoint(ctx, dev, stream, steps):

@@ -86,3 +86,19 @@ def diff_frame(seed: int, poison: bool = False, H: int = 512, W: int = 512):
 
 def diff_batch(n: int = 16, seed0: int = 200, poison: bool = False):
     return [diff_frame(seed0 + i, poison=poison) for i in range(n)]
+
+
+def line_problem(H: int, poison: bool = False):
+    """The line problem of the complexity validation (Section 7): image domain
+    [0, 4] x [0, 1] rendered at (4H) x H px (pixel centres), a horizontal line
+    0.45 <= y <= 0.55 of one colour on a background of another, hole
+    D = [0.4, 3.96] x [0.2, 0.8]; no splines (guide field 0), smart order off."""
+    W = 4 * H
+    xc = (np.arange(W, dtype=np.float64) + 0.5) * (4.0 / W)
+    yc = (np.arange(H, dtype=np.float64) + 0.5) * (1.0 / H)
+    line = (yc >= 0.45) & (yc <= 0.55)
+    img = np.empty((H, W, 3), np.float32)
+    img[:] = np.array([0.1, 0.3, 0.8], np.float32)
+    img[line] = np.array([0.9, 0.2, 0.1], np.float32)
+    hole = ((yc >= 0.2) & (yc <= 0.8))[:, None] & ((xc >= 0.4) & (xc <= 3.96))[None, :]
+    return _finish(img, hole, poison=poison, guide=np.zeros((H, W, 2), np.float32), smart=False)

@@ -325,3 +325,18 @@ def test_autotuned_launch_gives_identical_results():
         filled = o["shell"] >= 0
         assert np.abs(o["u"][filled] - outs[i].cpu().numpy()[filled]).max() <= 1e-4
     ctx.close()
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("H", [70, 140])
+def test_line_problem_of_the_complexity_validation(H):
+    """Section 7's line problem (onion order, no splines) at the two smallest
+    sizes of the complexity sweep: tracked and rescanned fills against the oracle."""
+    d = configs.line_problem(H, poison=True)
+    o = oracle_fill(d["rgb"], d["labels"], d["guide"], smart=False)
+    for rescan in (False, True):
+        r = gpu_fill(d["rgb"], d["labels"], d["guide"], smart=False, rescan=rescan)
+        assert_parity(o, r, d["labels"])
+    # onion order on a rectangle: one Chebyshev ring per step from both long sides
+    rows = int(d["labels"].any(axis=1).sum())
+    assert o["stats"]["shells"] == (rows + 1) // 2
