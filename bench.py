@@ -350,12 +350,13 @@ def main():
         e2e = {"value": world * fe / w, "unit": "filled px/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                "ms_per_step": w * 1e3, "call": "gf_fill_batched_host (pinned host buffers, splines in)"}
 
-    extra4k = adjoint = single = complexity = None
+    extra4k = adjoint = single = complexity = theorem1 = None
     if rank == 0 and not args.no_extra:
         single = leg_1080(ctx, dev, stream, max(10, args.extra_steps))
         extra4k = leg_4k(ctx, dev, stream, args.extra_steps)
         adjoint = leg_adjoint(ctx, dev, stream, args.extra_steps)
         complexity = leg_complexity(ctx, dev, stream, args.extra_steps)
+        theorem1 = leg_theorem1(dev)
 
     if rank != 0:
         if dist:
@@ -374,7 +375,7 @@ def main():
         "plain": plain, "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
         "gpu_launches": launches_per_step * K, "clocks": clocks,
         "single_1080": single, "tracked_vs_rescan_4k": extra4k, "adjoint_16x512": adjoint,
-        "complexity_line": complexity,
+        "complexity_line": complexity, "theorem1_curves": theorem1,
         "status_errors": bad,
     }
     print(json.dumps(line), flush=True)
@@ -552,6 +553,82 @@ def leg_complexity(ctx, dev, stream, steps):
         "paper": "alpha 0.54 / 1.10 and beta 0.5 / 1.0 with / without tracking on a GTX 970M",
         "workload": "line problem of Section 7 at 280x70 ... 4000x1000 px, eps=3, smart order off, g = 0",
     }
+
+
+def _theorem1_gstar(theta_deg, mu, r, ghost):
+    """Theorem 1 (eqs. limitDirection, ctgf_limits): the limiting transport
+    direction is the weighted centre of mass of the samples of the ball of radius
+    r lying in rows already filled (half-plane problem of Section 4, data below)."""
+    import math
+    th = math.radians(theta_deg)
+    gh = (math.cos(th), math.sin(th))
+    gp = (-gh[1], gh[0])
+    sx = sy = sw = 0.0
+    coef = mu * mu / (2.0 * r * r)
+    for m in range(-r, r + 1):
+        for n in range(-r, r + 1):
+            if (n, m) == (0, 0) or n * n + m * m > r * r:
+                continue
+            if ghost:
+                px, py, proj = n * gh[0] + m * gp[0], n * gh[1] + m * gp[1], m
+            else:
+                px, py, proj = n, m, -gh[1] * n + gh[0] * m
+            if py < 1.0:
+                continue
+            w = math.exp(-coef * proj * proj) / math.hypot(n, m)
+            sx, sy, sw = sx + w * px, sy + w * py, sw + w
+    return sx / sw, sy / sw
+
+
+def leg_theorem1(dev):
+    """Theorem 1 curves theta*(theta) measured from the CUDA fill: a straight edge
+    in the data below a half-plane hole, constant guidance at angle theta, onion
+    order; theta* from the per-row drift of the edge centroid, for the rotated
+    ball (Guidefill) and the lattice ball (coherence transport) at r = 3, 5."""
+    import math
+
+    import numpy as np
+    import torch
+
+    import synth
+    import paper_1611_05319_gb300 as gf
+    H, W, data_rows, mu = 64, 480, 8, 50.0
+    thetas = list(range(40, 141, 5))
+    ctx = gf.Context(dev.index)
+    hole = np.zeros((H, W), bool)
+    hole[: H - data_rows] = True
+    lab = torch.from_numpy(synth.labels_from(hole)).to(dev)
+    xs, ys = np.arange(W)[None, :], np.arange(H)[:, None]
+    imgs, guides = [], []
+    for th in thetas:
+        s_data = math.cos(math.radians(th)) / math.sin(math.radians(th))
+        u = (xs < W / 2.0 + s_data * (ys - (H - 1))).astype(np.float32)
+        imgs.append(torch.from_numpy(synth.to_rgba(np.repeat(u[..., None], 3, axis=2))).to(dev))
+        guides.append(torch.from_numpy(synth.const_guide(H, W, float(th))).to(dev))
+    rows = list(range(6, H - data_rows - 12))
+    lo, hi = int(W * 0.3), int(W * 0.7)
+    out = {"thetas": thetas}
+    for r in (3, 5):
+        for ghost in (True, False):
+            res = ctx.fill_batched(imgs, [lab] * len(thetas), guides, eps=float(r), mu=mu, smart=False, ghost=ghost)
+            meas, theo = [], []
+            for th, rr in zip(thetas, res):
+                f = rr.rgba[..., 0].double().cpu().numpy()
+                cents = []
+                for y in rows:
+                    pw = (f[y, :-1] - f[y, 1:])[lo:hi]
+                    cents.append(np.sum(pw * (np.arange(lo, hi) + 0.5)) / np.sum(pw))
+                slope = np.polyfit(np.array(rows, float), np.array(cents), 1)[0]
+                gx, gy = _theorem1_gstar(th, mu, r, ghost)
+                meas.append(math.degrees(math.atan2(1.0, slope)))
+                theo.append(math.degrees(math.atan2(gy, gx)))
+            key = ("guidefill" if ghost else "coherence_transport") + f"_r{r}"
+            out[key] = {"theta_star": [round(v, 3) for v in meas],
+                        "max_dev_from_theorem_deg": float(np.max(np.abs(np.array(meas) - np.array(theo)))),
+                        "max_kink_deg": float(np.max(np.abs(np.array(meas) - np.array(thetas))))}
+    ctx.close()
+    out["workload"] = f"{W}x{H} half-plane problem, {data_rows} data rows, step edge, mu={mu}, onion order"
+    return out
 
 
 def leg_adjoint(ctx, dev, stream, steps):
