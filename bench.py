@@ -271,6 +271,9 @@ def main():
         dist.barrier()
     clocks = clk.stop() if clk else None
     launch = "cluster %d x %d" % ctx.last_launch()
+    sm_, scs_, snc_ = ctx.last_split()
+    if sm_:
+        launch += "; the %d largest holes on a second launch of %d clusters of %d" % (sm_, snc_, scs_)
     ms = t0.elapsed_time(t1) / K
     fill_ms = statistics.mean(a.elapsed_time(b) for a, b in ev_fill)
     from paper_1611_05319_gb300.shard import max_over_ranks
@@ -281,7 +284,7 @@ def main():
     bad = [int(s) for s in st["status"] if s < 0]
     chunks = (n + 127) // 128
     # guidance: descriptor upload(s), bin, guide; fill: descriptor upload(s), init, order, persistent fill
-    launches_per_step = (chunks + 2) + (chunks + 3)
+    launches_per_step = (chunks + 2) + (chunks + 3) + (1 if sm_ else 0)  # + the second fill launch of a split
 
     # ---- plain per-frame fills (same frames, one gf_fill call each, no graph)
     plain = None

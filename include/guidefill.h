@@ -269,13 +269,30 @@ gf_status gf_fill_backward(gf_ctx *ctx, int n, const gf_adjoint_frame *frames, c
 gf_status gf_set_launch_config(gf_ctx *ctx, int cluster_size, int n_clusters, int use_graph);
 
 /*
+ * Split schedule of the batched fill (no counterpart in the paper; a tuning knob
+ * of this implementation).  The frames are taken largest hole first; with
+ * split_m > 0 the first split_m of them go to a second persistent launch of
+ * n_clusters clusters of cluster_size CTAs (1, 2, 4, 8 or 16), which runs beside
+ * the launch set by gf_set_launch_config on the SMs it leaves free.  Frames with
+ * long shell chains then get more CTAs each.  split_m = 0 turns the split off.
+ * A split that does not fit (too few frames or SMs) falls back to one launch.
+ * Results do not depend on the schedule.
+ */
+gf_status gf_set_split(gf_ctx *ctx, int split_m, int cluster_size, int n_clusters);
+
+/* Split schedule used by the last fill call (all zero: one launch). */
+gf_status gf_get_last_split(const gf_ctx *ctx, int *split_m, int *cluster_size, int *n_clusters);
+
+/*
  * Autotuner (no counterpart in the paper): fills these frames under every
  * schedulable cluster size (1, 2, 4, 8, 16 CTAs per frame, as many persistent
- * clusters as fit), `trials` timed runs each (CUDA events around the fill
- * kernel), and records the fastest shape in the context for later automatic
- * fills of frames with the same sizes, count, flags and ceil(eps).  The frames
- * are filled by every trial.  Synchronises `stream`.  Optional outputs: the
- * chosen cluster size and its mean fill-kernel time in ms.
+ * clusters as fit), then under split schedules (the m = 1, 2, 4, 8 largest holes
+ * on m or m/2 clusters of 8 or 16 CTAs beside the best uniform launch), `trials`
+ * timed runs each (CUDA events around the fill), and records the fastest
+ * schedule in the context for later automatic fills of frames with the same
+ * sizes, count, flags and ceil(eps).  The frames are filled by every trial.
+ * Synchronises `stream`.  Optional outputs: the chosen cluster size of the main
+ * launch and the mean fill time in ms.
  */
 gf_status gf_autotune(gf_ctx *ctx, int n, const gf_frame *frames, const gf_params *params,
                       gf_stats *dev_stats, void *stream, int trials, int *best_cluster_size,

@@ -95,6 +95,16 @@ class Context:
         check(lib().gf_get_last_launch(self._h, C.byref(a), C.byref(b)), "gf_get_last_launch")
         return a.value, b.value
 
+    def set_split(self, split_m: int = 0, cluster_size: int = 0, n_clusters: int = 0):
+        """Split schedule: the split_m largest holes on n_clusters clusters of
+        cluster_size CTAs beside the main launch (split_m = 0: one launch)."""
+        check(lib().gf_set_split(self._h, split_m, cluster_size, n_clusters), "gf_set_split")
+
+    def last_split(self):
+        m, a, b = C.c_int(), C.c_int(), C.c_int()
+        check(lib().gf_get_last_split(self._h, C.byref(m), C.byref(a), C.byref(b)), "gf_get_last_split")
+        return m.value, a.value, b.value
+
     def autotune(self, frames, stats: torch.Tensor, params, trials: int = 3, stream=None):
         """Runs gf_autotune on prepared ctypes frames; returns (cluster_size, ms)."""
         cs, ms = C.c_int(), C.c_float()

@@ -25,7 +25,7 @@ STATUS = {0: "ok", 1: "incomplete", -1: "invalid argument", -2: "CUDA error", -3
 EXPORTS = ["gf_create", "gf_destroy", "gf_status_string", "gf_last_cuda_error", "gf_fill",
            "gf_fill_batched", "gf_fill_batched_ex", "gf_fill_batched_host", "gf_guidance_from_splines", "gf_guidance_batched",
            "gf_set_launch_config", "gf_get_last_launch", "gf_max_active_clusters", "gf_fill_backward",
-           "gf_guide_from_angle", "gf_autotune", "gf_fill_noalloc"]
+           "gf_guide_from_angle", "gf_autotune", "gf_fill_noalloc", "gf_set_split", "gf_get_last_split"]
 
 
 class Frame(C.Structure):
@@ -109,6 +109,10 @@ def lib() -> C.CDLL:
         L.gf_autotune.restype = C.c_int
         L.gf_fill_noalloc.argtypes = [C.POINTER(Frame), C.POINTER(Params), P, P]
         L.gf_fill_noalloc.restype = C.c_int
+        L.gf_set_split.argtypes = [P, C.c_int, C.c_int, C.c_int]
+        L.gf_set_split.restype = C.c_int
+        L.gf_get_last_split.argtypes = [P, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int)]
+        L.gf_get_last_split.restype = C.c_int
         _lib = L
     return _lib
 

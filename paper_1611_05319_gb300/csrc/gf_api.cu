@@ -36,10 +36,18 @@ struct gf_ctx {
     int n_clusters = 0;
     int use_graph = 1;
     int last_cluster_size = 0, last_n_clusters = 0;
+    // split schedule (0 = none): the split_m frames with the largest holes go to a
+    // second persistent launch of split_nc clusters of split_cs CTAs, beside the
+    // launch that takes the other frames
+    int split_m = 0, split_cs = 0, split_nc = 0;
+    int last_split_m = 0, last_split_cs = 0, last_split_nc = 0;
+    cudaStream_t aux = nullptr;                   // the second launch's stream
+    cudaEvent_t fork_ev = nullptr, join_ev = nullptr;
     // autotuned launch shapes keyed by (n frames, H, W, eps, flags)
     struct Tuned {
         uint64_t key;
         int cluster_size, n_clusters;
+        int split_m, split_cs, split_nc;
         float ms;
     };
     std::vector<Tuned> tuned;
@@ -252,6 +260,14 @@ gf_status gf_create(gf_ctx **out, int device)
             return GF_ERR_CUDA;
         }
     }
+    e = cudaStreamCreateWithFlags(&ctx->aux, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->fork_ev, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->join_ev, cudaEventDisableTiming);
+    if (e != cudaSuccess) {
+        ctx->last_cuda = (int)e;
+        gf_destroy(ctx);
+        return GF_ERR_CUDA;
+    }
     *out = ctx;
     return GF_OK;
 }
@@ -260,6 +276,9 @@ void gf_destroy(gf_ctx *ctx)
 {
     if (!ctx) return;
     cudaSetDevice(ctx->device);
+    if (ctx->aux) cudaStreamDestroy(ctx->aux);
+    if (ctx->fork_ev) cudaEventDestroy(ctx->fork_ev);
+    if (ctx->join_ev) cudaEventDestroy(ctx->join_ev);
     cudaDeviceSynchronize();
     drop_graphs(ctx, nullptr);
     if (ctx->arena.ptr) cudaFree(ctx->arena.ptr);
@@ -290,6 +309,27 @@ gf_status gf_get_last_launch(const gf_ctx *ctx, int *cluster_size, int *n_cluste
     if (!ctx || !cluster_size || !n_clusters) return GF_ERR_ARG;
     *cluster_size = ctx->last_cluster_size;
     *n_clusters = ctx->last_n_clusters;
+    return GF_OK;
+}
+
+gf_status gf_set_split(gf_ctx *ctx, int split_m, int cluster_size, int n_clusters)
+{
+    if (!ctx || split_m < 0 || n_clusters < 0) return GF_ERR_ARG;
+    if (split_m > 0 && cluster_size != 1 && cluster_size != 2 && cluster_size != 4 && cluster_size != 8 &&
+        cluster_size != 16)
+        return GF_ERR_ARG;
+    ctx->split_m = split_m;
+    ctx->split_cs = split_m > 0 ? cluster_size : 0;
+    ctx->split_nc = split_m > 0 ? n_clusters : 0;
+    return GF_OK;
+}
+
+gf_status gf_get_last_split(const gf_ctx *ctx, int *split_m, int *cluster_size, int *n_clusters)
+{
+    if (!ctx || !split_m || !cluster_size || !n_clusters) return GF_ERR_ARG;
+    *split_m = ctx->last_split_m;
+    *cluster_size = ctx->last_split_cs;
+    *n_clusters = ctx->last_split_nc;
     return GF_OK;
 }
 
@@ -342,19 +382,25 @@ static gf_status enqueue_fill(gf_ctx *ctx, int n, const gf_frame *frames, const 
     const size_t off_icnt = pos; pos = align_up(pos + 8 * (size_t)n, 256);
     const size_t off_desc = pos; pos = align_up(pos + sizeof(FrameDev) * (size_t)n, 256);
     const size_t off_order = pos; pos = align_up(pos + 4 * (size_t)n, 256);
-    const size_t off_cursor = pos; pos = align_up(pos + 4, 256);
+    const size_t off_cursor = pos; pos = align_up(pos + 8, 256);  // queue heads of the two launches
     const size_t off_ctaoff = pos; pos = align_up(pos + 4 * (size_t)(n + 1), 256);
 
     // ---- launch shape
     const int rw = rw_for(prm->eps);
     int cs = ctx->cluster_size;
     int tuned_nc = 0;
+    int sm = ctx->split_m, scs = ctx->split_cs, snc = ctx->split_nc;
     if (cs == 0) {
         const uint64_t tk = tune_key(n, frames, prm);
         for (const auto &t : ctx->tuned)
             if (t.key == tk) {
                 cs = t.cluster_size;
                 tuned_nc = t.n_clusters;
+                if (sm == 0) {
+                    sm = t.split_m;
+                    scs = t.split_cs;
+                    snc = t.split_nc;
+                }
             }
     }
     if (cs == 0) cs = (n == 1) ? 16 : 2;
@@ -365,12 +411,27 @@ static gf_status enqueue_fill(gf_ctx *ctx, int n, const gf_frame *frames, const 
     }
     if (maxc <= 0) return GF_ERR_UNSUPPORTED;
     int nc = ctx->n_clusters > 0 ? std::min(ctx->n_clusters, maxc) : (tuned_nc > 0 ? std::min(tuned_nc, maxc) : maxc);
-    nc = std::max(1, std::min(nc, n));
+    // split schedule: the second launch takes snc clusters of scs CTAs (one CTA per
+    // SM) for the sm largest holes; the first launch keeps the SMs left over
+    bool split = sm > 0 && sm < n && scs > 0 && snc > 0;
+    if (split) {
+        const int maxa = gf_max_active_clusters(ctx, prm->eps, scs);
+        snc = std::min(std::min(snc, sm), maxa);
+        const int spare = snc > 0 ? (ctx->sm_count - snc * scs) / cs : 0;
+        if (snc <= 0 || spare < 1) split = false;
+        else nc = std::min(nc, spare);
+    }
+    if (!split) sm = scs = snc = 0;
+    nc = std::max(1, std::min(nc, n - sm));
     ctx->last_cluster_size = cs;
     ctx->last_n_clusters = nc;
+    ctx->last_split_m = sm;
+    ctx->last_split_cs = scs;
+    ctx->last_split_nc = snc;
+    const int ncall = nc + snc;  // control blocks and work lists of both launches
 
-    const size_t off_ctl = pos; pos = align_up(pos + sizeof(GroupCtl) * (size_t)nc, 256);
-    const size_t off_lists = pos; pos = align_up(pos + 4 * (size_t)3 * list_cap * nc, 256);
+    const size_t off_ctl = pos; pos = align_up(pos + sizeof(GroupCtl) * (size_t)ncall, 256);
+    const size_t off_lists = pos; pos = align_up(pos + 4 * (size_t)3 * list_cap * ncall, 256);
     gf_status st = ensure(ctx, ctx->arena, pos);
     if (st != GF_OK) return st;
     char *A = (char *)ctx->arena.ptr;
@@ -424,7 +485,8 @@ static gf_status enqueue_fill(gf_ctx *ctx, int n, const gf_frame *frames, const 
     fp.coef64 = (double)prm->mu * (double)prm->mu / (2.0 * (double)prm->eps * (double)prm->eps);
     fp.c64 = (double)prm->c;
     fp.flags = prm->flags;
-    fp.n_frames = n;
+    fp.n_frames = n - sm;  // the first launch: frame_order[sm ..)
+    fp.order_first = sm;
     fp.list_cap = list_cap;
     fp.frames = (FrameDev *)(A + off_desc);
     fp.frame_order = (int32_t *)(A + off_order);
@@ -432,6 +494,12 @@ static gf_status enqueue_fill(gf_ctx *ctx, int n, const gf_frame *frames, const 
     fp.groups = (GroupCtl *)(A + off_ctl);
     fp.lists = (int32_t *)(A + off_lists);
     build_tab(prm->eps, fp.tab);
+    FillParams fpa = fp;  // the second launch: frame_order[0 .. sm)
+    fpa.n_frames = sm;
+    fpa.order_first = 0;
+    fpa.frame_cursor = fp.frame_cursor + 1;
+    fpa.groups = fp.groups + nc;
+    fpa.lists = fp.lists + (size_t)nc * 3 * list_cap;
 
     // graph key: everything the enqueued work depends on
     uint64_t key = 1469598103934665603ull;
@@ -439,6 +507,9 @@ static gf_status enqueue_fill(gf_ctx *ctx, int n, const gf_frame *frames, const 
     key = fnv(key, prm, sizeof(*prm));
     key = fnv(key, &cs, sizeof(cs));
     key = fnv(key, &nc, sizeof(nc));
+    key = fnv(key, &sm, sizeof(sm));
+    key = fnv(key, &scs, sizeof(scs));
+    key = fnv(key, &snc, sizeof(snc));
     key = fnv(key, &n, sizeof(n));
     for (int i = 0; i < n; i++) key = fnv(key, &frames[i].rgba, sizeof(void *));
     key = fnv(key, &ctx->arena.ptr, sizeof(void *));
@@ -490,7 +561,7 @@ static gf_status enqueue_fill(gf_ctx *ctx, int n, const gf_frame *frames, const 
         if (e) break;
         e = cudaMemsetAsync(A + off_icnt, 0, 8 * (size_t)n, stream);
         if (e) break;
-        e = cudaMemsetAsync(A + off_ctl, 0, sizeof(GroupCtl) * (size_t)nc, stream);
+        e = cudaMemsetAsync(A + off_ctl, 0, sizeof(GroupCtl) * (size_t)ncall, stream);
         if (e) break;
         for (int i = 0; i < n && !e; i++) {
             const gf_frame &f = frames[i];
@@ -519,10 +590,29 @@ static gf_status enqueue_fill(gf_ctx *ctx, int n, const gf_frame *frames, const 
         if (g1) cudaGraphDestroy(g1);
         return cuda_fail(ctx, e);
     }
+    // phase 2: the persistent fill, or with a split schedule the two persistent
+    // launches side by side (the second on the context's own stream, forked from
+    // and joined back into `stream`; neither waits for the other)
+    auto launch_phase2 = [&]() -> cudaError_t {
+        if (!split) return launch_fill(rw, cfg, fp);
+        cudaError_t r = cudaEventRecord(ctx->fork_ev, stream);
+        if (r == cudaSuccess) r = cudaStreamWaitEvent(ctx->aux, ctx->fork_ev, 0);
+        cudaLaunchConfig_t cfga = cfg;
+        cudaLaunchAttribute ata[1] = {at[0]};
+        ata[0].val.clusterDim.x = scs;
+        cfga.attrs = ata;
+        cfga.gridDim = dim3((unsigned)(snc * scs));
+        cfga.stream = ctx->aux;
+        if (r == cudaSuccess) r = launch_fill(rw, cfga, fpa);
+        if (r == cudaSuccess) r = launch_fill(rw, cfg, fp);
+        if (r == cudaSuccess) r = cudaEventRecord(ctx->join_ev, ctx->aux);
+        if (r == cudaSuccess) r = cudaStreamWaitEvent(stream, ctx->join_ev, 0);
+        return r;
+    };
     if (!graph) {
         // ---- phase 2 directly
         if (ev0) CK(cudaEventRecord(ev0, stream));
-        CK(launch_fill(rw, cfg, fp));
+        CK(launch_phase2());
         if (ev1) CK(cudaEventRecord(ev1, stream));
         return GF_OK;
     }
@@ -530,7 +620,7 @@ static gf_status enqueue_fill(gf_ctx *ctx, int n, const gf_frame *frames, const 
     cudaGraph_t g2 = nullptr;
     e = cudaStreamBeginCapture(stream, cudaStreamCaptureModeThreadLocal);
     if (e == cudaSuccess) {
-        e = launch_fill(rw, cfg, fp);
+        e = launch_phase2();
         cudaError_t e2 = cudaStreamEndCapture(stream, &g2);
         if (e == cudaSuccess) e = e2;
     }
@@ -572,10 +662,12 @@ gf_status gf_fill_batched(gf_ctx *ctx, int n, const gf_frame *frames, const gf_p
     return gf_fill_batched_ex(ctx, n, frames, params, dev_stats, stream, nullptr, nullptr);
 }
 
-/* Times the batched fill of these frames under candidate launch shapes
- * (cluster sizes 1..16, as many clusters as fit) and keeps the fastest for
- * later calls on frames of the same sizes and parameters.  The frames are
- * filled (in place if out_rgba == rgba) by every trial.  Synchronises stream. */
+/* Times the batched fill of these frames under candidate launch shapes and keeps
+ * the fastest for later calls on frames of the same sizes and parameters:
+ * uniform schedules (cluster sizes 1..16, as many clusters as fit), then split
+ * schedules (the m = 1, 2, 4, 8 largest holes on m or m/2 clusters of 8 or 16
+ * CTAs beside the best uniform launch).  The frames are filled (in place if
+ * out_rgba == rgba) by every trial.  Synchronises stream. */
 gf_status gf_autotune(gf_ctx *ctx, int n, const gf_frame *frames, const gf_params *params, gf_stats *dev_stats,
                       void *stream, int trials, int *best_cluster_size, float *best_ms)
 {
@@ -591,40 +683,78 @@ gf_status gf_autotune(gf_ctx *ctx, int n, const gf_frame *frames, const gf_param
     cudaStream_t st = (cudaStream_t)stream;
     if (trials <= 0) trials = 3;
     const int save_cs = ctx->cluster_size, save_nc = ctx->n_clusters;
+    const int save_sm = ctx->split_m, save_scs = ctx->split_cs, save_snc = ctx->split_nc;
     cudaEvent_t e0, e1;
     CK(cudaEventCreate(&e0));
     CK(cudaEventCreate(&e1));
-    int best_cs = 0, best_nc = 0;
+    // mean fill-kernel time of one schedule over `trials` runs (after a capture run)
+    auto measure = [&](float *avg) -> gf_status {
+        gf_status r = enqueue_fill(ctx, n, frames, params, dev_stats, st);  // warm-up / capture
+        float tot = 0.f;
+        for (int t = 0; t < trials && r == GF_OK; t++) {
+            r = enqueue_fill(ctx, n, frames, params, dev_stats, st, e0, e1);
+            if (r != GF_OK) break;
+            cudaError_t ee = cudaEventSynchronize(e1);
+            float ms = 0.f;
+            if (ee == cudaSuccess) ee = cudaEventElapsedTime(&ms, e0, e1);
+            if (ee != cudaSuccess) r = cuda_fail(ctx, ee);
+            tot += ms;
+        }
+        *avg = tot / trials;
+        return r;
+    };
+    // uniform schedules: one cluster size for every frame
+    int best_cs = 0, best_nc = 0, best_sm = 0, best_scs = 0, best_snc = 0;
     float best = 1e30f;
+    ctx->split_m = ctx->split_cs = ctx->split_nc = 0;
     for (int cs : {1, 2, 4, 8, 16}) {
         if (gf_max_active_clusters(ctx, params->eps, cs) <= 0) continue;
         ctx->cluster_size = cs;
         ctx->n_clusters = 0;
-        s = enqueue_fill(ctx, n, frames, params, dev_stats, st);  // warm-up / capture
+        float avg = 0.f;
+        s = measure(&avg);
         if (s != GF_OK) break;
-        float tot = 0.f;
-        for (int t = 0; t < trials && s == GF_OK; t++) {
-            s = enqueue_fill(ctx, n, frames, params, dev_stats, st, e0, e1);
-            if (s != GF_OK) break;
-            e = cudaEventSynchronize(e1);
-            float ms = 0.f;
-            if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
-            if (e != cudaSuccess) {
-                s = cuda_fail(ctx, e);
-                break;
-            }
-            tot += ms;
-        }
-        if (s != GF_OK) break;
-        const float avg = tot / trials;
         if (avg < best) {
             best = avg;
             best_cs = cs;
             best_nc = ctx->last_n_clusters;
         }
     }
+    // split schedules: the frames with the largest holes (whose shell chains are
+    // usually the longest) on a few larger clusters, the rest on the best uniform
+    // cluster size with the SMs left over
+    if (s == GF_OK && best_cs > 0 && n > 1) {
+        ctx->cluster_size = best_cs;
+        ctx->n_clusters = 0;
+        for (int m : {1, 2, 4, 8}) {
+            if (m >= n || s != GF_OK) break;
+            for (int scs : {8, 16}) {
+                if (scs <= best_cs || s != GF_OK) continue;
+                const int cands[2] = {m, (m + 1) / 2};
+                for (int ci = 0; ci < (cands[1] == cands[0] ? 1 : 2); ci++) {
+                    const int snc = cands[ci];
+                    ctx->split_m = m;
+                    ctx->split_cs = scs;
+                    ctx->split_nc = snc;
+                    float avg = 0.f;
+                    s = measure(&avg);
+                    if (s != GF_OK) break;
+                    if (ctx->last_split_m == m && avg < best) {
+                        best = avg;
+                        best_nc = ctx->last_n_clusters;
+                        best_sm = m;
+                        best_scs = scs;
+                        best_snc = ctx->last_split_nc;
+                    }
+                }
+            }
+        }
+    }
     ctx->cluster_size = save_cs;
     ctx->n_clusters = save_nc;
+    ctx->split_m = save_sm;
+    ctx->split_cs = save_scs;
+    ctx->split_nc = save_snc;
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     if (s != GF_OK) return s;
@@ -635,10 +765,13 @@ gf_status gf_autotune(gf_ctx *ctx, int n, const gf_frame *frames, const gf_param
         if (t.key == tk) {
             t.cluster_size = best_cs;
             t.n_clusters = best_nc;
+            t.split_m = best_sm;
+            t.split_cs = best_scs;
+            t.split_nc = best_snc;
             t.ms = best;
             found = true;
         }
-    if (!found) ctx->tuned.push_back({tk, best_cs, best_nc, best});
+    if (!found) ctx->tuned.push_back({tk, best_cs, best_nc, best_sm, best_scs, best_snc, best});
     if (best_cluster_size) *best_cluster_size = best_cs;
     if (best_ms) *best_ms = best;
     return GF_OK;

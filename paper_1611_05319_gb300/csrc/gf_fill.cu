@@ -5,7 +5,9 @@
 //                 per 8x8 tile the bitmask of hole pixels (U) and of the initial
 //                 active boundary (Qw = d_active D^(0)_h, Notation) built with
 //                 warp ballots, per-frame hole count.
-//   order_kernel  sorts frames by hole size (largest first) into the work queue.
+//   order_kernel  sorts frames by hole size (largest first) into the work queue
+//                 (a split schedule gives its first frames to a second launch
+//                 with larger clusters, running beside the first).
 //   fill_kernel   persistent; one thread-block cluster runs one frame's whole
 //                 shell loop (Algorithm 1) at a time, with one hardware cluster
 //                 barrier per step, then takes the next frame from the queue.
@@ -188,7 +190,7 @@ __global__ void order_kernel(const FrameDev *frames, int n, int32_t *order, int3
         }
         order[rank] = i;
     }
-    if (blockIdx.x == 0 && threadIdx.x == 0) *cursor = 0;
+    if (blockIdx.x == 0 && threadIdx.x < 2) cursor[threadIdx.x] = 0;
 }
 
 // ---------------------------------------------------------------------------
@@ -898,7 +900,7 @@ __global__ void __launch_bounds__(fill_warps(RW) * 32, 1) fill_kernel(const __gr
         cluster.sync();
         const int f = __ldcg(&ctl->cur_frame[it & 1]);
         if (f >= p.n_frames) break;
-        if (threadIdx.x == 0) s_frame = p.frames[p.frame_order[f]];
+        if (threadIdx.x == 0) s_frame = p.frames[p.frame_order[p.order_first + f]];
         __syncthreads();
         const FrameDev &F = s_frame;
 

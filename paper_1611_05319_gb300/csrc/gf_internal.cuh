@@ -109,11 +109,12 @@ struct FillParams {
     double coef64;                // mu^2 / (2 eps^2), FP64 (same expression as the host)
     double c64;
     uint32_t flags;
-    int32_t n_frames;
+    int32_t n_frames;             // frames of this launch: frame_order[order_first .. order_first + n_frames)
     int32_t list_cap;             // capacity of each work list (max ntiles)
+    int32_t order_first;
     FrameDev *frames;
-    int32_t *frame_order;         // frames in processing order (device)
-    int32_t *frame_cursor;        // device work queue head
+    int32_t *frame_order;         // all frames of the request, largest hole first (device)
+    int32_t *frame_cursor;        // this launch's work queue head
     GroupCtl *groups;             // one per cluster
     int32_t *lists;               // [n_clusters][3][list_cap]
     SampleTab tab;
@@ -219,6 +220,8 @@ __global__ void upload_splines_kernel(const __grid_constant__ SplineChunk c);
 const void *fill_kernel_entry(int rw);
 cudaError_t launch_fill(int rw, const cudaLaunchConfig_t &cfg, const FillParams &p);
 __global__ void init_kernel(const __grid_constant__ InitArgs a);
+// sorts the frames by hole size (largest first) into `order`; clears the two
+// work-queue heads cursor[0..1]
 __global__ void order_kernel(const FrameDev *frames, int n, int32_t *order, int32_t *cursor);
 __global__ void angle_kernel(int64_t npx, const uint8_t *labels, const float *mag, const float *phi,
                              float2 *guide);

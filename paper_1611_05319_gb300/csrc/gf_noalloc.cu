@@ -62,7 +62,7 @@ constexpr Layout layout(int64_t T)
     l.icnt = p; p = up256(p + 8);
     l.desc = p; p = up256(p + sizeof(FrameDev));
     l.order = p; p = up256(p + 4);
-    l.cursor = p; p = up256(p + 4);
+    l.cursor = p; p = up256(p + 8);  // two queue heads (order_kernel clears both)
     l.ctaoff = p; p = up256(p + 8);
     l.ctl = p; p = up256(p + sizeof(GroupCtl));
     l.lists = p; p = up256(p + 4 * 3 * 9 * (size_t)T);  // three work lists of 9 slots per tile

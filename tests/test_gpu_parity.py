@@ -340,3 +340,38 @@ def test_line_problem_of_the_complexity_validation(H):
     # onion order on a rectangle: one Chebyshev ring per step from both long sides
     rows = int(d["labels"].any(axis=1).sum())
     assert o["stats"]["shells"] == (rows + 1) // 2
+
+
+def test_split_schedule_gives_identical_results():
+    """The split schedule (largest holes on a second launch of larger clusters,
+    beside the main launch) fills every frame exactly as one launch does."""
+    import torch
+
+    import paper_1611_05319_gb300 as gf
+    frames = [_case(40 + 8 * i, 48 + 4 * i, 900 + i) for i in range(9)]
+    dev = torch.device("cuda", 0)
+    outs = []
+    for split in ((0, 0, 0), (3, 8, 2), (1, 16, 1)):
+        ctx = gf.Context(0)
+        ctx.set_launch_config(2, 0)
+        ctx.set_split(*split)
+        rs = ctx.fill_batched([torch.from_numpy(rgba(im)).to(dev) for im, _, _ in frames],
+                              [torch.from_numpy(lb).to(dev) for _, lb, _ in frames],
+                              [torch.from_numpy(g).to(dev) for _, _, g in frames], eps=3.0, mu=10.0, enter=True)
+        torch.cuda.synchronize()
+        outs.append(([r.shell.cpu().numpy() for r in rs], [r.rgba.cpu().numpy() for r in rs],
+                     [r.enter.cpu().numpy() for r in rs], [r.stats() for r in rs]))
+        m, cs, nc = ctx.last_split()
+        assert (m, cs) == (split[0], split[1]) and (nc > 0) == (split[0] > 0)
+        ctx.close()
+    for o in outs[1:]:
+        for a, b in zip(outs[0][0], o[0]):
+            assert np.array_equal(a, b)
+        for a, b in zip(outs[0][1], o[1]):
+            assert np.array_equal(a, b, equal_nan=True)
+        for a, b in zip(outs[0][2], o[2]):
+            assert np.array_equal(a, b)
+        for a, b in zip(outs[0][3], o[3]):
+            assert (a["shells"], a["filled"], a["status"]) == (b["shells"], b["filled"], b["status"])
+    o = oracle_fill(*frames[8], eps=3.0, mu=10.0)
+    assert np.array_equal(o["shell"], outs[1][0][8])
