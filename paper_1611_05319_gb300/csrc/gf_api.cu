@@ -665,8 +665,8 @@ gf_status gf_fill_batched(gf_ctx *ctx, int n, const gf_frame *frames, const gf_p
 /* Times the batched fill of these frames under candidate launch shapes and keeps
  * the fastest for later calls on frames of the same sizes and parameters:
  * uniform schedules (cluster sizes 1..16, as many clusters as fit), then split
- * schedules (the m = 1, 2, 4, 8 largest holes on m or m/2 clusters of 8 or 16
- * CTAs beside the best uniform launch).  The frames are filled (in place if
+ * schedules (the m = 1, 2, 4, 8, 12, 16, 24 largest holes on m or m/2 clusters
+ * of 8 or 16 CTAs beside the best uniform launch).  The frames are filled (in place if
  * out_rgba == rgba) by every trial.  Synchronises stream. */
 gf_status gf_autotune(gf_ctx *ctx, int n, const gf_frame *frames, const gf_params *params, gf_stats *dev_stats,
                       void *stream, int trials, int *best_cluster_size, float *best_ms)
@@ -726,7 +726,7 @@ gf_status gf_autotune(gf_ctx *ctx, int n, const gf_frame *frames, const gf_param
     if (s == GF_OK && best_cs > 0 && n > 1) {
         ctx->cluster_size = best_cs;
         ctx->n_clusters = 0;
-        for (int m : {1, 2, 4, 8}) {
+        for (int m : {1, 2, 4, 8, 12, 16, 24}) {
             if (m >= n || s != GF_OK) break;
             for (int scs : {8, 16}) {
                 if (scs <= best_cs || s != GF_OK) continue;
