@@ -403,7 +403,7 @@ static gf_status enqueue_fill(gf_ctx *ctx, int n, const gf_frame *frames, const 
                 }
             }
     }
-    if (cs == 0) cs = (n == 1) ? 16 : 2;
+    if (cs == 0) cs = (n == 1) ? 16 : 4;  // before any autotuning: 16 CTAs for one frame, 4 per frame of a batch
     int maxc = gf_max_active_clusters(ctx, prm->eps, cs);
     while (maxc <= 0 && cs > 1) {
         cs /= 2;
