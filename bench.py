@@ -40,16 +40,16 @@ WORKLOAD = ("batched: 64 frames 1920x1080 RGBA fp32 (seeds 100-163), holes U[0.5
 SEED0, NFRAMES = 100, 64
 
 # DRAM traffic of fill_kernel per filled pixel from one ncu capture of the first 8
-# frames of this batch (dram__bytes_read.sum + dram__bytes_write.sum = 36.373504 MB +
-# 0.758784 MB for 534,164 filled pixels; profiles/fill_kernel_batch_8x1080.md).  It
+# frames of this batch (dram__bytes_read.sum + dram__bytes_write.sum = 36.395008 MB +
+# 0.713216 MB for 534,164 filled pixels; profiles/fill_kernel_batch_8x1080.md).  It
 # holds only for the kernel sources it was taken on: with any other source the
 # roofline's traffic is reported as null.
 FILL_TRAFFIC = {
     "sources": {
-        "paper_1611_05319_gb300/csrc/gf_fill.cu": "79b12a18d1f01057e6450256d7996e00e56c590e1496349c9c6e7e44c2748bc8",
-        "paper_1611_05319_gb300/csrc/gf_internal.cuh": "4ea9308c7bcf24250d5036e22588937919faf72d7edb3120393bdf8805cebbac",
+        "paper_1611_05319_gb300/csrc/gf_fill.cu": "57daefb50935397dd7dc744052d584c02aace6959f798e8b19c677262e0fd142",
+        "paper_1611_05319_gb300/csrc/gf_internal.cuh": "a7a4405e602ffc8cb68d1d887739c383302d7c3fe61b95ea0f9f8a2e2571145e",
     },
-    "bytes_per_filled_px": (36.373504e6 + 0.758784e6) / 534164,
+    "bytes_per_filled_px": (36.395008e6 + 0.713216e6) / 534164,
 }
 
 
