@@ -43,6 +43,9 @@ struct gf_ctx {
     int last_split_m = 0, last_split_cs = 0, last_split_nc = 0;
     cudaStream_t aux = nullptr;                   // the second launch's stream
     cudaEvent_t fork_ev = nullptr, join_ev = nullptr;
+    // host-buffer path: copy streams and the events of its chunk pipeline
+    cudaStream_t copy_in = nullptr, copy_out = nullptr;
+    std::vector<cudaEvent_t> pipe_ev;
     // autotuned launch shapes keyed by (n frames, H, W, eps, flags)
     struct Tuned {
         uint64_t key;
@@ -261,6 +264,8 @@ gf_status gf_create(gf_ctx **out, int device)
         }
     }
     e = cudaStreamCreateWithFlags(&ctx->aux, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&ctx->copy_in, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&ctx->copy_out, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->fork_ev, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->join_ev, cudaEventDisableTiming);
     if (e != cudaSuccess) {
@@ -277,6 +282,9 @@ void gf_destroy(gf_ctx *ctx)
     if (!ctx) return;
     cudaSetDevice(ctx->device);
     if (ctx->aux) cudaStreamDestroy(ctx->aux);
+    if (ctx->copy_in) cudaStreamDestroy(ctx->copy_in);
+    if (ctx->copy_out) cudaStreamDestroy(ctx->copy_out);
+    for (cudaEvent_t ev : ctx->pipe_ev) cudaEventDestroy(ev);
     if (ctx->fork_ev) cudaEventDestroy(ctx->fork_ev);
     if (ctx->join_ev) cudaEventDestroy(ctx->join_ev);
     cudaDeviceSynchronize();
@@ -361,7 +369,7 @@ int gf_max_active_clusters(gf_ctx *ctx, float eps, int cluster_size)
 
 static gf_status enqueue_fill(gf_ctx *ctx, int n, const gf_frame *frames, const gf_params *prm,
                               gf_stats *dev_stats, cudaStream_t stream, cudaEvent_t ev0 = nullptr,
-                              cudaEvent_t ev1 = nullptr)
+                              cudaEvent_t ev1 = nullptr, bool allow_graph = true)
 {
     // ---- layout of the scratch arena
     std::vector<size_t> off_U(n), off_Q(n), off_F(n), off_S(n), off_L(n);
@@ -514,7 +522,7 @@ static gf_status enqueue_fill(gf_ctx *ctx, int n, const gf_frame *frames, const 
     for (int i = 0; i < n; i++) key = fnv(key, &frames[i].rgba, sizeof(void *));
     key = fnv(key, &ctx->arena.ptr, sizeof(void *));
 
-    const bool graph = ctx->use_graph && stream != nullptr;
+    const bool graph = allow_graph && ctx->use_graph && stream != nullptr;
     if (graph && ctx->gexec && ctx->gexec_fill && ctx->gkey == key) {
         CK(cudaGraphLaunch(ctx->gexec, stream));
         if (ev0) CK(cudaEventRecord(ev0, stream));
@@ -1081,31 +1089,31 @@ gf_status gf_fill_batched_host(gf_ctx *ctx, int n, const int32_t *H, const int32
     if (s != GF_OK) return s;
     char *A = (char *)ctx->io.ptr;
     cudaStream_t st = (cudaStream_t)stream;
-    std::vector<gf_frame> fr(n);
-    std::vector<gf_spline_frame> sf;
-    for (int i = 0; i < n; i++) {
-        size_t np = (size_t)H[i] * W[i];
-        CK(cudaMemcpyAsync(A + o_rgba[i], host_rgba[i], 16 * np, cudaMemcpyHostToDevice, st));
-        CK(cudaMemcpyAsync(A + o_lab[i], host_labels[i], np, cudaMemcpyHostToDevice, st));
-        if (!from_splines[i]) {
-            CK(cudaMemcpyAsync(A + o_g[i], host_guide[i], 8 * np, cudaMemcpyHostToDevice, st));
-        } else {
-            if (n_splines[i] > 0) {
-                CK(cudaMemcpyAsync(A + o_off[i], host_offsets[i], 4 * (size_t)(n_splines[i] + 1),
-                                   cudaMemcpyHostToDevice, st));
-                CK(cudaMemcpyAsync(A + o_pts[i], host_pts[i], 8 * (size_t)n_points[i], cudaMemcpyHostToDevice, st));
-            }
-            gf_spline_frame g;
-            g.H = H[i]; g.W = W[i];
-            g.labels = (const uint8_t *)(A + o_lab[i]);
-            g.n_splines = n_splines[i];
-            g.n_points = n_points[i];
-            g.offsets = (const int32_t *)(A + o_off[i]);
-            g.pts = (const float *)(A + o_pts[i]);
-            g.guide = (float *)(A + o_g[i]);
-            sf.push_back(g);
-        }
-        gf_frame &f = fr[i];
+    // Chunk pipeline: the frames' inputs are copied in on one stream, each chunk is
+    // filled on `stream` as soon as its inputs have landed, and its outputs are
+    // copied out on a third stream while later chunks are still being filled, so
+    // the copies in both directions overlap each other and the compute.
+    const int nchunk = std::min(n, 4);
+    // frames are dealt to the chunks round-robin (position q of the pipeline order
+    // holds frame perm[q]), so that frames with long shell chains spread over them
+    std::vector<int> perm;
+    perm.reserve(n);
+    for (int c = 0; c < nchunk; c++)
+        for (int i = c; i < n; i += nchunk) perm.push_back(i);
+    while ((int)ctx->pipe_ev.size() < 2 * nchunk + 2) {
+        cudaEvent_t ev;
+        CK(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+        ctx->pipe_ev.push_back(ev);
+    }
+    cudaEvent_t ev_start = ctx->pipe_ev[0], ev_out_done = ctx->pipe_ev[1];
+    CK(cudaEventRecord(ev_start, st));  // inputs may be written by work already on `stream`
+    CK(cudaStreamWaitEvent(ctx->copy_in, ev_start, 0));
+    CK(cudaStreamWaitEvent(ctx->copy_out, ev_start, 0));
+    std::vector<gf_frame> fr(n);  // in pipeline order
+    std::vector<gf_spline_frame> sf(n);
+    for (int q = 0; q < n; q++) {
+        const int i = perm[q];
+        gf_frame &f = fr[q];
         f.H = H[i]; f.W = W[i];
         f.rgba = (const float *)(A + o_rgba[i]);
         f.labels = (const uint8_t *)(A + o_lab[i]);
@@ -1114,20 +1122,78 @@ gf_status gf_fill_batched_host(gf_ctx *ctx, int n, const int32_t *H, const int32
         f.out_shell = (int32_t *)(A + o_sh[i]);
         f.out_enter = nullptr;
         f.out_stall = nullptr;
+        gf_spline_frame &g = sf[q];
+        g.H = H[i]; g.W = W[i];
+        g.labels = (const uint8_t *)(A + o_lab[i]);
+        g.n_splines = from_splines[i] ? n_splines[i] : 0;
+        g.n_points = from_splines[i] ? n_points[i] : 0;
+        g.offsets = (const int32_t *)(A + o_off[i]);
+        g.pts = (const float *)(A + o_pts[i]);
+        g.guide = (float *)(A + o_g[i]);
     }
-    if (!sf.empty()) {
-        s = gf_guidance_batched(ctx, (int)sf.size(), sf.data(), eta, stream);
-        if (s != GF_OK) return s;
+    for (int c = 0; c < nchunk; c++) {
+        const int q0 = n * c / nchunk, q1 = n * (c + 1) / nchunk;
+        for (int q = q0; q < q1; q++) {
+            const int i = perm[q];
+            size_t np = (size_t)H[i] * W[i];
+            CK(cudaMemcpyAsync(A + o_rgba[i], host_rgba[i], 16 * np, cudaMemcpyHostToDevice, ctx->copy_in));
+            CK(cudaMemcpyAsync(A + o_lab[i], host_labels[i], np, cudaMemcpyHostToDevice, ctx->copy_in));
+            if (!from_splines[i]) {
+                CK(cudaMemcpyAsync(A + o_g[i], host_guide[i], 8 * np, cudaMemcpyHostToDevice, ctx->copy_in));
+            } else if (n_splines[i] > 0) {
+                CK(cudaMemcpyAsync(A + o_off[i], host_offsets[i], 4 * (size_t)(n_splines[i] + 1),
+                                   cudaMemcpyHostToDevice, ctx->copy_in));
+                CK(cudaMemcpyAsync(A + o_pts[i], host_pts[i], 8 * (size_t)n_points[i], cudaMemcpyHostToDevice,
+                                   ctx->copy_in));
+            }
+        }
+        CK(cudaEventRecord(ctx->pipe_ev[2 + 2 * c], ctx->copy_in));
     }
-    s = enqueue_fill(ctx, n, fr.data(), params, (gf_stats *)(A + o_st), st);
-    if (s != GF_OK) return s;
-    for (int i = 0; i < n; i++) {
-        size_t np = (size_t)H[i] * W[i];
-        CK(cudaMemcpyAsync(host_out_rgba[i], A + o_rgba[i], 16 * np, cudaMemcpyDeviceToHost, st));
-        CK(cudaMemcpyAsync(host_out_shell[i], A + o_sh[i], 4 * np, cudaMemcpyDeviceToHost, st));
+    // Unless a launch shape was set, a chunk's frames get the largest cluster size at
+    // which every one of them has its own cluster (8 CTAs for 16 frames on 152 SMs).
+    const int save_cs = ctx->cluster_size;
+    gf_status fs = GF_OK;
+    for (int c = 0; c < nchunk && fs == GF_OK; c++) {
+        const int q0 = n * c / nchunk, q1 = n * (c + 1) / nchunk;
+        CK(cudaStreamWaitEvent(st, ctx->pipe_ev[2 + 2 * c], 0));
+        std::vector<gf_spline_frame> sfc;
+        for (int q = q0; q < q1; q++)
+            if (from_splines[perm[q]]) sfc.push_back(sf[q]);
+        if (!sfc.empty()) {
+            fs = gf_guidance_batched(ctx, (int)sfc.size(), sfc.data(), eta, stream);
+            if (fs != GF_OK) break;
+        }
+        if (save_cs == 0) {
+            int cs = 16;
+            while (cs > 1 && cs * (q1 - q0) > ctx->sm_count) cs >>= 1;
+            ctx->cluster_size = cs;
+        }
+        // graphs are keyed by the frame set, which changes from chunk to chunk
+        fs = enqueue_fill(ctx, q1 - q0, fr.data() + q0, params, (gf_stats *)(A + o_st) + q0, st, nullptr, nullptr,
+                          false);
+        ctx->cluster_size = save_cs;
+        if (fs != GF_OK) break;
+        CK(cudaEventRecord(ctx->pipe_ev[3 + 2 * c], st));
+        CK(cudaStreamWaitEvent(ctx->copy_out, ctx->pipe_ev[3 + 2 * c], 0));
+        for (int q = q0; q < q1; q++) {
+            const int i = perm[q];
+            size_t np = (size_t)H[i] * W[i];
+            CK(cudaMemcpyAsync(host_out_rgba[i], A + o_rgba[i], 16 * np, cudaMemcpyDeviceToHost, ctx->copy_out));
+            CK(cudaMemcpyAsync(host_out_shell[i], A + o_sh[i], 4 * np, cudaMemcpyDeviceToHost, ctx->copy_out));
+        }
     }
-    CK(cudaMemcpyAsync(host_stats, A + o_st, sizeof(gf_stats) * (size_t)n, cudaMemcpyDeviceToHost, st));
+    CK(cudaEventRecord(ev_out_done, ctx->copy_out));
+    CK(cudaStreamWaitEvent(st, ev_out_done, 0));
+    if (fs != GF_OK) {
+        cudaStreamSynchronize(ctx->copy_in);
+        cudaStreamSynchronize(ctx->copy_out);
+        cudaStreamSynchronize(st);
+        return fs;
+    }
+    std::vector<gf_stats> st_q(n);
+    CK(cudaMemcpyAsync(st_q.data(), A + o_st, sizeof(gf_stats) * (size_t)n, cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
+    for (int q = 0; q < n; q++) host_stats[perm[q]] = st_q[q];
     return GF_OK;
 }
 
