@@ -353,13 +353,14 @@ def main():
         e2e = {"value": world * fe / w, "unit": "filled px/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                "ms_per_step": w * 1e3, "call": "gf_fill_batched_host (pinned host buffers, splines in)"}
 
-    extra4k = adjoint = single = complexity = theorem1 = None
+    extra4k = adjoint = single = complexity = theorem1 = data_term = None
     if rank == 0 and not args.no_extra:
         single = leg_1080(ctx, dev, stream, max(10, args.extra_steps))
         extra4k = leg_4k(ctx, dev, stream, args.extra_steps)
         adjoint = leg_adjoint(ctx, dev, stream, args.extra_steps)
         complexity = leg_complexity(ctx, dev, stream, args.extra_steps)
         theorem1 = leg_theorem1(dev)
+        data_term = leg_data_term(ctx, dev, stream, max(3, args.extra_steps))
 
     if rank != 0:
         if dist:
@@ -378,7 +379,7 @@ def main():
         "plain": plain, "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
         "gpu_launches": launches_per_step * K, "clocks": clocks,
         "single_1080": single, "tracked_vs_rescan_4k": extra4k, "adjoint_16x512": adjoint,
-        "complexity_line": complexity, "theorem1_curves": theorem1,
+        "complexity_line": complexity, "theorem1_curves": theorem1, "data_term_1080": data_term,
         "status_errors": bad,
     }
     print(json.dumps(line), flush=True)
@@ -631,6 +632,49 @@ def leg_theorem1(dev):
                         "max_kink_deg": float(np.max(np.abs(np.array(meas) - np.array(thetas))))}
     ctx.close()
     out["workload"] = f"{W}x{H} half-plane problem, {data_rows} data rows, step edge, mu={mu}, onion order"
+    return out
+
+
+def leg_data_term(ctx, dev, stream, steps):
+    """The data term of eq. ready2 on the single 1080p frame (guide field from its
+    splines): fill-kernel time, shells and the step at which eq. ready takes over,
+    beside the fill without it."""
+    import ctypes as C
+
+    import numpy as np
+    import torch
+
+    from synth import configs, to_rgba
+    from paper_1611_05319_gb300 import _lib
+    f = configs.frame_1080()
+    H, W = f["labels"].shape
+    lab = torch.from_numpy(f["labels"]).to(dev)
+    img = torch.from_numpy(to_rgba(f["rgb"])).to(dev)
+    g = ctx.guidance(lab, f["splines"][0], f["splines"][1], 3.0)
+    shell = torch.empty((H, W), dtype=torch.int32, device=dev)
+    stats = torch.zeros((_lib.STATS_BYTES,), dtype=torch.uint8, device=dev)
+    fr = (_lib.Frame * 1)(_lib.Frame(H, W, img.data_ptr(), lab.data_ptr(), g.data_ptr(), img.data_ptr(),
+                                     shell.data_ptr(), None, None))
+    L = _lib.lib()
+    sp = C.c_void_p(stream.cuda_stream)
+    out = {}
+    for name, dt in (("plain", False), ("data_term", True)):
+        prm = _lib.make_params(eps=3.0, mu=50.0, c=0.05, data_term=dt)
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        for a, b in evs:
+            a.record(stream)
+            b.record(stream)
+        for k in range(steps + 1):
+            e = evs[k - 1] if k > 0 else None
+            _lib.check(L.gf_fill_batched_ex(ctx._h, 1, fr, C.byref(prm), C.c_void_p(stats.data_ptr()), sp,
+                                            C.c_void_p(e[0].cuda_event) if e else None,
+                                            C.c_void_p(e[1].cuda_event) if e else None), "fill", ctx._h)
+        torch.cuda.synchronize()
+        st = np.frombuffer(stats.cpu().numpy().tobytes(), dtype=_lib.STATS_DTYPE)[0]
+        out[name] = {"fill_kernel_ms": float(np.median([a.elapsed_time(b) for a, b in evs])),
+                     "shells": int(st["shells"]), "stalls": int(st["stalls"]), "data_switch": int(st["data_switch"]),
+                     "filled": int(st["filled"])}
+    out["workload"] = "1920x1080 frame of the single-frame case (seed 2), eps=3, mu=50, guide field from its splines"
     return out
 
 

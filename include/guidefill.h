@@ -56,6 +56,9 @@ typedef enum {
 #define GF_FLAG_GHOST 1u  /* rotated ghost-pixel ball (Guidefill); off = lattice ball (coherence transport) */
 #define GF_FLAG_SMART 2u  /* smart order, ready = C(x) > c (eq. ready); off = onion order */
 #define GF_FLAG_RESCAN 4u /* recompute the whole active boundary every step ("without tracking", Section 3.6) */
+#define GF_FLAG_DATA 8u   /* data term D(x) = |g(x)| of eq. ready2 (Section 3.5, possible extensions): while
+                             some hole pixel with g != 0 is unfilled, only pixels with g != 0 are ready; eq.
+                             ready from the first step at which none is left or none would be filled */
 
 /* Opaque library context. */
 typedef struct gf_ctx gf_ctx;
@@ -106,6 +109,8 @@ typedef struct {
     int64_t evaluations; /* ready tests executed (implementation count) */
     int64_t max_front;   /* max over k of |d_active D^(k)_h| */
     int64_t holes;       /* |D_h| */
+    int32_t data_switch; /* GF_FLAG_DATA: first step evaluated with eq. ready (-1: flag off or never) */
+    int32_t reserved;
 } gf_stats;
 
 /* Creates a context bound to CUDA device `device` (must be compute capability

@@ -27,6 +27,7 @@ _LIB = os.path.join(_HERE, "liboracle.so")
 
 GHOST = 1
 SMART = 2
+DATA = 8  # data term of eq. ready2
 
 KNOWN, UNFILLED, BYSTANDER = -1, -2, -3
 
@@ -34,7 +35,7 @@ KNOWN, UNFILLED, BYSTANDER = -1, -2, -3
 class Stats(C.Structure):
     _fields_ = [("shells", C.c_int32), ("stalls", C.c_int32), ("evaluations", C.c_int64),
                 ("filled", C.c_int64), ("unreachable", C.c_int64), ("max_front", C.c_int64),
-                ("min_margin", C.c_double)]
+                ("min_margin", C.c_double), ("data_switch", C.c_int32), ("pad", C.c_int32)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -87,7 +88,7 @@ def _f32(x):
 
 
 def fill(rgb, labels, guide, eps=3.0, mu=50.0, c=0.05, ghost=True, smart=True, tau=1e-5,
-         max_shells=0):
+         max_shells=0, data_term=False):
     """Runs Algorithm 1 on a copy of ``rgb`` (float32/64 [H, W, C]) in FP64.
     Parameters are rounded to FP32 first (the library takes FP32 parameters).
     Returns dict(u=float64 [H, W, C], shell, enter, stall_steps, stats, status)."""
@@ -103,7 +104,7 @@ def fill(rgb, labels, guide, eps=3.0, mu=50.0, c=0.05, ghost=True, smart=True, t
     cap = max_shells if max_shells > 0 else n_hole + 1
     stall = np.zeros(cap + 1, np.uint8)
     st = Stats()
-    flags = (GHOST if ghost else 0) | (SMART if smart else 0)
+    flags = (GHOST if ghost else 0) | (SMART if smart else 0) | (DATA if data_term else 0)
     rc = lib().oracle_fill(H, W, Cn, _p(u), _p(lab), _p(g), _f32(eps), _f32(mu), _f32(c), flags,
                            _f32(tau), int(max_shells), _p(shell), _p(enter), _p(stall),
                            C.byref(st))

@@ -53,6 +53,7 @@
 
 #define OF_GHOST 1u
 #define OF_SMART 2u
+#define OF_DATA 8u /* data term D(x) = |g(x)| of eq. ready2 (Section 3.5, possible extensions) */
 
 #define MAX_SAMPLES 1024
 
@@ -64,6 +65,8 @@ typedef struct {
     int64_t unreachable;  /* hole pixels never filled */
     int64_t max_front;    /* max_k |front_k| */
     double min_margin;    /* min over smart-order decisions of |C - c| / c */
+    int32_t data_switch;  /* eq. ready2: first step evaluated with eq. ready (-1: no data term) */
+    int32_t pad;
 } oracle_stats;
 
 /* ---------------------------------------------------------------------- */
@@ -319,7 +322,14 @@ int oracle_fill(int H, int W, int C, double *u, const uint8_t *lab, const float 
     int32_t *front = (int32_t *)malloc(sizeof(int32_t) * (N > 0 ? N : 1));
     double *newc = (double *)malloc(sizeof(double) * (N > 0 ? N : 1) * C);
     uint8_t *rdy = (uint8_t *)malloc(N > 0 ? N : 1);
+    uint8_t *rdy0 = (uint8_t *)malloc(N > 0 ? N : 1);
     int64_t filled = 0;
+    /* eq. ready2 (Section 3.5, possible extensions): while phase 1 lasts, a front
+     * pixel is ready only if also D(x) = |g(x)| > c2 = 0.  Phase 1 ends at the first
+     * step at which no unfilled hole pixel has g != 0, or at which it would fill
+     * nothing (that step is then evaluated with eq. ready); from then on eq. ready. */
+    int phase1 = (flags & OF_DATA) != 0;
+    st->data_switch = -1;
     int k;
     for (k = 0; k < max_shells; k++) {
         size_t nf = 0;
@@ -329,18 +339,37 @@ int oracle_fill(int H, int W, int C, double *u, const uint8_t *lab, const float 
         if (nf == 0) break;
         if ((int64_t)nf > st->max_front) st->max_front = (int64_t)nf;
         st->evaluations += (int64_t)nf;
+        if (phase1) {
+            int64_t gleft = 0;
+            for (size_t p = 0; p < N; p++)
+                if (shell[p] == SH_UNFILLED && (guide[2 * p] != 0.0f || guide[2 * p + 1] != 0.0f)) gleft++;
+            if (gleft == 0) {
+                phase1 = 0;
+                st->data_switch = k;
+            }
+        }
         size_t nready = 0;
         for (size_t i = 0; i < nf; i++) {
             int p = front[i];
             if (enter && enter[p] < 0) enter[p] = k;
             double conf;
             int any;
-            rdy[i] = (uint8_t)evaluate(F, p % W, p / W, k, 0, &newc[i * C], &conf, &any);
+            rdy0[i] = (uint8_t)evaluate(F, p % W, p / W, k, 0, &newc[i * C], &conf, &any);
             if ((flags & OF_SMART) && c > 0) {
                 double mg = fabs(conf - c) / c;
                 if (mg < st->min_margin) st->min_margin = mg;
             }
+            rdy[i] = rdy0[i];
+            if (phase1 && guide[2 * (size_t)p] == 0.0f && guide[2 * (size_t)p + 1] == 0.0f) rdy[i] = 0;
             nready += rdy[i];
+        }
+        if (phase1 && nready == 0) {
+            phase1 = 0;
+            st->data_switch = k;
+            for (size_t i = 0; i < nf; i++) {
+                rdy[i] = rdy0[i];
+                nready += rdy[i];
+            }
         }
         int stall = 0;
         if (nready == 0) { /* R7 */
@@ -372,6 +401,7 @@ int oracle_fill(int H, int W, int C, double *u, const uint8_t *lab, const float 
     free(front);
     free(newc);
     free(rdy);
+    free(rdy0);
     free(F);
     return st->unreachable > 0 ? 1 : 0;
 }

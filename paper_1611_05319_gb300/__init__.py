@@ -135,17 +135,19 @@ class Context:
         return fr, out_rgba, shell, enter, stall, keep
 
     def fill(self, rgba, labels, guide, eps=3.0, mu=50.0, c=0.05, ghost=True, smart=True, rescan=False,
-             snap_tau=1e-5, max_shells=0, out=None, enter=False, stall=False, stream=None) -> FillResult:
+             snap_tau=1e-5, max_shells=0, out=None, enter=False, stall=False, stream=None,
+             data_term=False) -> FillResult:
         """Fills one frame.  rgba [H,W,3|4] float32, labels [H,W] uint8 (0 known, 1 hole, 2 bystander),
         guide [H,W,2] float32.  out=None allocates the output, out="inplace" fills rgba in place
         (rgba must then already be a contiguous [H,W,4] float32 CUDA tensor)."""
         return self.fill_batched([rgba], [labels], [guide], eps, mu, c, ghost, smart, rescan, snap_tau, max_shells,
-                                 out=None if out is None else [out], enter=enter, stall=stall, stream=stream)[0]
+                                 out=None if out is None else [out], enter=enter, stall=stall, stream=stream,
+                                 data_term=data_term)[0]
 
     def fill_batched(self, rgba: Sequence[torch.Tensor], labels: Sequence[torch.Tensor],
                      guide: Sequence[torch.Tensor], eps=3.0, mu=50.0, c=0.05, ghost=True, smart=True,
                      rescan=False, snap_tau=1e-5, max_shells=0, out=None, enter=False, stall=False,
-                     stream=None) -> List[FillResult]:
+                     stream=None, data_term=False) -> List[FillResult]:
         n = len(rgba)
         if not (len(labels) == len(guide) == n) or n == 0:
             raise ValueError("rgba, labels and guide must have the same non-zero length")
@@ -158,7 +160,7 @@ class Context:
             keep.append(kp)
             res.append((o, sh, en, st))
         stats = torch.empty((n * STATS_BYTES,), dtype=torch.uint8, device=torch.device("cuda", self.device))
-        prm = make_params(eps, mu, c, ghost, smart, rescan, snap_tau, max_shells)
+        prm = make_params(eps, mu, c, ghost, smart, rescan, snap_tau, max_shells, data_term)
         with torch.cuda.device(self.device):
             check(lib().gf_fill_batched(self._h, n, frames, C.byref(prm), _ptr(stats), _stream(stream)),
                   "gf_fill_batched", self._h)
@@ -168,7 +170,7 @@ class Context:
 
     def fill_frames(self, frames, stats: torch.Tensor, params, stream=None, events=None):
         """Lowest-overhead batched call: ``frames`` is a prepared ctypes array of
-        _lib.Frame, ``stats`` a device buffer of n*48 bytes, ``params`` a _lib.Params;
+        _lib.Frame, ``stats`` a device buffer of n*56 bytes (_lib.STATS_BYTES each), ``params`` a _lib.Params;
         ``events`` an optional pair of recorded torch.cuda.Event placed around the
         persistent fill kernel."""
         e0 = C.c_void_p(events[0].cuda_event) if events else None
@@ -255,7 +257,7 @@ class Context:
                           guide: Optional[Sequence[Optional[np.ndarray]]], out_rgba: Sequence[np.ndarray],
                           out_shell: Sequence[np.ndarray], splines=None, eta=3.0, eps=3.0, mu=50.0, c=0.05,
                           ghost=True, smart=True, rescan=False, snap_tau=1e-5, max_shells=0,
-                          stream=None) -> np.ndarray:
+                          stream=None, data_term=False) -> np.ndarray:
         """Fills frames held in HOST memory (numpy; rgba [H,W,4] float32, labels [H,W] uint8,
         guide [H,W,2] float32 or None with ``splines[i] = (offsets, pts)``); the library
         copies them to the device, fills, and copies out_rgba / out_shell back.
@@ -285,7 +287,7 @@ class Context:
                 ns[i] = len(o) - 1
                 npts[i] = p.shape[0]
         st = np.zeros(n, dtype=STATS_DTYPE)
-        prm = make_params(eps, mu, c, ghost, smart, rescan, snap_tau, max_shells)
+        prm = make_params(eps, mu, c, ghost, smart, rescan, snap_tau, max_shells, data_term)
         with torch.cuda.device(self.device):
             check(lib().gf_fill_batched_host(self._h, n, Hs, Ws, arr(rgba), arr(labels), arr(guide), ns, arr(offs),
                                              npts, arr(pts), C.c_float(eta), arr(out_rgba), arr(out_shell),

@@ -16,6 +16,7 @@ LIB_PATH = os.path.join(HERE, "libguidefill.so")
 GF_FLAG_GHOST = 1
 GF_FLAG_SMART = 2
 GF_FLAG_RESCAN = 4
+GF_FLAG_DATA = 8
 
 STATUS = {0: "ok", 1: "incomplete", -1: "invalid argument", -2: "CUDA error", -3: "timeout",
           -4: "no progress", -5: "out of memory", -6: "unsupported device", -7: "internal error",
@@ -52,8 +53,8 @@ class AdjointFrame(C.Structure):
 
 STATS_DTYPE = np.dtype([("shells", np.int32), ("stalls", np.int32), ("status", np.int32), ("rechecks", np.int32),
                         ("filled", np.int64), ("evaluations", np.int64), ("max_front", np.int64),
-                        ("holes", np.int64)])
-STATS_BYTES = STATS_DTYPE.itemsize  # 48
+                        ("holes", np.int64), ("data_switch", np.int32), ("reserved", np.int32)])
+STATS_BYTES = STATS_DTYPE.itemsize  # 56
 
 
 class GuidefillError(RuntimeError):
@@ -126,6 +127,8 @@ def check(code: int, what: str, ctx=None):
     return code
 
 
-def make_params(eps=3.0, mu=50.0, c=0.05, ghost=True, smart=True, rescan=False, snap_tau=1e-5, max_shells=0):
-    flags = (GF_FLAG_GHOST if ghost else 0) | (GF_FLAG_SMART if smart else 0) | (GF_FLAG_RESCAN if rescan else 0)
+def make_params(eps=3.0, mu=50.0, c=0.05, ghost=True, smart=True, rescan=False, snap_tau=1e-5, max_shells=0,
+                data_term=False):
+    flags = (GF_FLAG_GHOST if ghost else 0) | (GF_FLAG_SMART if smart else 0) | (GF_FLAG_RESCAN if rescan else 0) | \
+        (GF_FLAG_DATA if data_term else 0)
     return Params(float(eps), float(mu), float(c), flags, float(snap_tau), int(max_shells))

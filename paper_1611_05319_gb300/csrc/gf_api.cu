@@ -187,7 +187,7 @@ static gf_status check_params(const gf_params *p)
     if (!p) return GF_ERR_ARG;
     if (!(p->eps >= 1.0f && p->eps <= 7.0f)) return GF_ERR_ARG;
     if (!(p->mu >= 0.0f) || !std::isfinite(p->mu)) return GF_ERR_ARG;
-    if (p->flags & ~(GF_FLAG_GHOST | GF_FLAG_SMART | GF_FLAG_RESCAN)) return GF_ERR_ARG;
+    if (p->flags & ~(GF_FLAG_GHOST | GF_FLAG_SMART | GF_FLAG_RESCAN | GF_FLAG_DATA)) return GF_ERR_ARG;
     if ((p->flags & GF_FLAG_SMART) && !(p->c >= 1e-6f && p->c < 1.0f)) return GF_ERR_ARG;
     if (!(p->snap_tau >= 0.0f && p->snap_tau < 0.01f)) return GF_ERR_ARG;
     if (p->max_shells < 0) return GF_ERR_ARG;
@@ -387,6 +387,7 @@ static gf_status enqueue_fill(gf_ctx *ctx, int n, const gf_frame *frames, const 
         off_L[i] = pos; pos = align_up(pos + 4 * (size_t)ntiles[i], 256);
     }
     const size_t off_holes = pos; pos = align_up(pos + 4 * (size_t)n, 256);
+    const size_t off_gleft = pos; pos = align_up(pos + 4 * (size_t)n, 256);
     const size_t off_icnt = pos; pos = align_up(pos + 8 * (size_t)n, 256);
     const size_t off_desc = pos; pos = align_up(pos + sizeof(FrameDev) * (size_t)n, 256);
     const size_t off_order = pos; pos = align_up(pos + 4 * (size_t)n, 256);
@@ -474,6 +475,7 @@ static gf_status enqueue_fill(gf_ctx *ctx, int n, const gf_frame *frames, const 
         d.F = (TileF *)(A + off_F[i]);
         d.sched = (int32_t *)(A + off_S[i]);
         d.holes = (int32_t *)(A + off_holes) + i;
+        d.gleft = (int32_t *)(A + off_gleft) + i;
         d.init_list = (int32_t *)(A + off_L[i]);
         d.init_count = (int32_t *)(A + off_icnt) + 2 * i;
         hd[i] = d;
@@ -566,6 +568,7 @@ static gf_status enqueue_fill(gf_ctx *ctx, int n, const gf_frame *frames, const 
         }
         if (e) break;
         e = cudaMemsetAsync(A + off_holes, 0, 4 * (size_t)n, stream);
+        if (!e) e = cudaMemsetAsync(A + off_gleft, 0, 4 * (size_t)n, stream);
         if (e) break;
         e = cudaMemsetAsync(A + off_icnt, 0, 8 * (size_t)n, stream);
         if (e) break;
@@ -583,6 +586,7 @@ static gf_status enqueue_fill(gf_ctx *ctx, int n, const gf_frame *frames, const 
         ia.frames = fp.frames;
         ia.cta_offset = (const int32_t *)(A + off_ctaoff);
         ia.n_frames = n;
+        ia.flags = prm->flags;
         init_kernel<<<(unsigned)ctas, 256, 0, stream>>>(ia);
         e = cudaGetLastError();
         if (e) break;

@@ -99,6 +99,8 @@ __global__ void __launch_bounds__(256) init_kernel(const __grid_constant__ InitA
 
     const int x = x0 + t;
     const int lane = t & 31;
+    const bool data = (a.flags & GF_FLAG_DATA) != 0;
+    int gcount = 0;  // data term: hole pixels of this warp's columns with g != 0
     unsigned long long Um[4] = {0, 0, 0, 0}, Qm[4] = {0, 0, 0, 0};
 #pragma unroll
     for (int r = 0; r < TILE; r++) {
@@ -120,6 +122,14 @@ __global__ void __launch_bounds__(256) init_kernel(const __grid_constant__ InitA
         if (in && F.enter) F.enter[(size_t)y * W + x] = front ? 0 : -1;  // optional map, plain stores
         unsigned hb = __ballot_sync(FULL, hole);
         unsigned fb = __ballot_sync(FULL, front);
+        if (data) {
+            bool gz = false;
+            if (hole) {
+                const float2 gv = __ldg(&F.guide[(size_t)y * W + x]);
+                gz = gv.x != 0.0f || gv.y != 0.0f;
+            }
+            gcount += __popc(__ballot_sync(FULL, gz));
+        }
 #pragma unroll
         for (int q = 0; q < 4; q++) {
             Um[q] |= (unsigned long long)((hb >> (8 * q)) & 0xffu) << (8 * r);
@@ -135,6 +145,7 @@ __global__ void __launch_bounds__(256) init_kernel(const __grid_constant__ InitA
                 *reinterpret_cast<int4 *>(F.shell + (size_t)y * W + x) = *reinterpret_cast<const int4 *>(&out_s[r][4 * c4]);
         }
     }
+    if (data && lane == 0 && gcount) atomicAdd(F.gleft, gcount);
     const int warp = t >> 5;
     bool has_front = false;
     int tile = 0, nq = 0;
@@ -196,7 +207,11 @@ __global__ void order_kernel(const FrameDev *frames, int n, int32_t *order, int3
 // ---------------------------------------------------------------------------
 // fill
 // ---------------------------------------------------------------------------
-enum Mode { NORMAL = 0, RESCAN = 1, STALL = 2 };
+// NORMAL: a work-list tile, candidates near the last step's fills.  RESCAN:
+// every unfilled pixel each step (no tracking).  STALL: the stall rule over the
+// waiting front.  REVAL: every unfilled pixel once with eq. ready (the step at
+// which the data term of eq. ready2 is switched off), with claims.
+enum Mode { NORMAL = 0, RESCAN = 1, STALL = 2, REVAL = 3 };
 
 __device__ __forceinline__ int nth_bit64(unsigned long long m, int q)
 {
@@ -406,7 +421,7 @@ __device__ __forceinline__ void claims_drain(const FillParams &p, GroupCtl *ctl,
 template <int RW, int MODE>
 __device__ void process_tile(const FillParams &p, const FrameDev &F, WarpSmem<RW> *ws, GroupCtl *ctl,
                              int32_t *lists, int t, int k, unsigned long long cand_in, WarpCounters &wc,
-                             PendingClaims &pc, bool defer)
+                             PendingClaims &pc, bool defer, bool phase1)
 {
     constexpr int WS = WarpSmem<RW>::WS;
     const int lane = threadIdx.x & 31;
@@ -726,6 +741,11 @@ __device__ void process_tile(const FillParams &p, const FrameDev &F, WarpSmem<RW
                 ready = d > tol;
                 recheck = !(d > tol) && !(d < -tol);
             }
+            if (phase1 && g.x == 0.0f && g.y == 0.0f) {
+                // eq. ready2, first phase: the data term D(x) = |g(x)| must exceed c2 = 0
+                ready = false;
+                recheck = false;
+            }
             if (act && j == 0 && cnt > 0 && (ready || recheck)) {
                 atomicOr(recheck ? &ws->recheck : &ws->ready, 1ull << pix);
                 const float inv = 1.0f / wsum;
@@ -744,6 +764,17 @@ __device__ void process_tile(const FillParams &p, const FrameDev &F, WarpSmem<RW
     __syncwarp();
     const unsigned long long Rm = ws->ready;
     const int nr = __popcll(Rm);
+    if (phase1) {
+        // guided pixels filled: the data term stays on while any is left
+        bool gz[2];
+#pragma unroll
+        for (int h = 0; h < 2; h++) {
+            const int pix = lane + 32 * h;
+            gz[h] = ((Rm >> pix) & 1ull) && (ws->guide[pix].x != 0.0f || ws->guide[pix].y != 0.0f);
+        }
+        const int ng = __popc(__ballot_sync(FULL, gz[0])) + __popc(__ballot_sync(FULL, gz[1]));
+        if (lane == 0 && ng) atomicSub(F.gleft, ng);
+    }
 
     // ---- the fills (state word k: not readable by any other test of step k)
 #pragma unroll
@@ -840,23 +871,25 @@ __device__ __forceinline__ void flush_counters(GroupCtl *ctl, const WarpCounters
     }
 }
 
-// Every warp of the cluster visits the frame's tiles (32 at a time); `which`
-// selects the tile mask that makes a tile a member (U: rescan, Qw: stall).
+// Every warp of the cluster visits the frame's tiles (32 at a time); the mode
+// selects the tile mask that makes a tile a member (U: rescan, re-evaluation;
+// Qw: stall) and is passed on as the tile's candidates.
 template <int RW, int MODE>
 __device__ void sweep_tiles(const FillParams &p, const FrameDev &F, WarpSmem<RW> *ws, GroupCtl *ctl,
-                            int32_t *lists, int k, int gw, int nw, WarpCounters &wc, PendingClaims &pc)
+                            int32_t *lists, int k, int gw, int nw, WarpCounters &wc, PendingClaims &pc,
+                            bool phase1 = false)
 {
     const int lane = threadIdx.x & 31;
     for (int base = gw * 32; base < F.ntiles; base += nw * 32) {
         int t = base + lane;
         unsigned long long m = 0;
-        if (t < F.ntiles) m = (MODE == RESCAN) ? __ldcg(&F.U[t]) : __ldcg(&F.Qw[t]);
+        if (t < F.ntiles) m = (MODE == RESCAN || MODE == REVAL) ? __ldcg(&F.U[t]) : __ldcg(&F.Qw[t]);
         unsigned bal = __ballot_sync(FULL, m != 0ull);
         while (bal) {
             int i = __ffs(bal) - 1;
             bal &= bal - 1;
             unsigned long long mi = __shfl_sync(FULL, m, i);
-            process_tile<RW, MODE>(p, F, ws, ctl, lists, base + i, k, mi, wc, pc, false);
+            process_tile<RW, MODE>(p, F, ws, ctl, lists, base + i, k, mi, wc, pc, false, phase1);
         }
     }
 }
@@ -913,6 +946,16 @@ __global__ void __launch_bounds__(fill_warps(RW) * 32, 1) fill_kernel(const __gr
         // ahead, together with the previous step's counters
         int n_cur = __ldcg(&F.init_count[0]);
         int t0_cur = gw < n_cur ? __ldcg(&F.init_list[gw]) : -1;
+        // eq. ready2 (GF_FLAG_DATA): phase 1 while hole pixels with g != 0 remain and
+        // some front pixel is ready under the data term; `reval`: this step tests every
+        // front pixel with eq. ready (the tracked front was built under phase 1)
+        bool phase1 = (p.flags & GF_FLAG_DATA) != 0;
+        int data_switch = -1;
+        bool reval = false;
+        if (phase1 && __ldcg(F.gleft) == 0) {
+            phase1 = false;
+            data_switch = 0;
+        }
         for (;;) {
             const int slot = k % 3;
             WarpCounters wc = {0, 0, 0, 0, 0};
@@ -920,7 +963,9 @@ __global__ void __launch_bounds__(fill_warps(RW) * 32, 1) fill_kernel(const __gr
             pc.m1 = 0u;
             pc.m2 = 0u;
             if (rescan) {
-                sweep_tiles<RW, RESCAN>(p, F, ws, ctl, lists, k, gw, nw, wc, pc);
+                sweep_tiles<RW, RESCAN>(p, F, ws, ctl, lists, k, gw, nw, wc, pc, phase1);
+            } else if (reval) {
+                sweep_tiles<RW, REVAL>(p, F, ws, ctl, lists, k, gw, nw, wc, pc);
             } else {
                 // step 0 takes the init kernel's list, later steps the lists built by the claims
                 const int n = n_cur;
@@ -934,13 +979,13 @@ __global__ void __launch_bounds__(fill_warps(RW) * 32, 1) fill_kernel(const __gr
                 int pre = 0;
                 if (lane0 && more) pre = atomicAdd(&ctl->cursor[slot], 1);
                 const int t0 = gw < n ? t0_cur : -1;
-                if (t0 >= 0) process_tile<RW, NORMAL>(p, F, ws, ctl, lists, t0, k, 0ull, wc, pc, more);
+                if (t0 >= 0) process_tile<RW, NORMAL>(p, F, ws, ctl, lists, t0, k, 0ull, wc, pc, more, phase1);
                 if (more) {
                     int nxt = nw + __shfl_sync(FULL, pre, 0);
                     while (nxt < n) {
                         const int t = __ldcg(&L[nxt]);
                         if (lane0) pre = atomicAdd(&ctl->cursor[slot], 1);
-                        if (t >= 0) process_tile<RW, NORMAL>(p, F, ws, ctl, lists, t, k, 0ull, wc, pc, more);
+                        if (t >= 0) process_tile<RW, NORMAL>(p, F, ws, ctl, lists, t, k, 0ull, wc, pc, more, phase1);
                         nxt = nw + __shfl_sync(FULL, pre, 0);
                     }
                 }
@@ -951,12 +996,13 @@ __global__ void __launch_bounds__(fill_warps(RW) * 32, 1) fill_kernel(const __gr
             // one round trip: this step's counters and the next step's list
             const int s3n = (k + 1) % 3;
             const int32_t *Ln = lists + (size_t)s3n * p.list_cap;
-            const int filled = __ldcg(&ctl->filled[slot]);
-            const int dlt = __ldcg(&ctl->front_delta[slot]);
+            int filled = __ldcg(&ctl->filled[slot]);
+            int dlt = __ldcg(&ctl->front_delta[slot]);
             const int ev = __ldcg(&ctl->evals[slot]);
             const int er = __ldcg(&ctl->err[slot]);
             int n_next = __ldcg(&ctl->list_count[s3n]);
             int t0_next = gw < p.list_cap ? __ldcg(&Ln[gw]) : -1;  // used only if gw < n_next
+            const int gleft = phase1 ? __ldcg(F.gleft) : -1;
             evals_tot += ev;
             if (er) {
                 status = GF_ERR_INTERNAL;
@@ -964,6 +1010,34 @@ __global__ void __launch_bounds__(fill_warps(RW) * 32, 1) fill_kernel(const __gr
             }
             long long front_k = n_front + dlt + filled;
             if (front_k > max_front) max_front = front_k;
+            reval = false;
+            if (phase1 && filled == 0) {
+                // eq. ready2 fills nothing at this step: eq. ready from this step on,
+                // and this step is evaluated again with it (every front pixel)
+                phase1 = false;
+                data_switch = k;
+                WarpCounters wr = {0, 0, 0, 0, 0};
+                sweep_tiles<RW, REVAL>(p, F, ws, ctl, lists, k, gw, nw, wr, pc);
+                claims_drain(p, ctl, lists, pc, wr);
+                flush_counters(ctl, wr, k, true, false);
+                cluster.sync();
+                filled = __ldcg(&ctl->filled[slot]);
+                dlt = __ldcg(&ctl->front_delta[slot]);
+                const int er1 = __ldcg(&ctl->err[slot]);
+                n_next = __ldcg(&ctl->list_count[s3n]);
+                t0_next = gw < p.list_cap ? __ldcg(&Ln[gw]) : -1;
+                if (er1) {
+                    status = GF_ERR_INTERNAL;
+                    break;
+                }
+                front_k = n_front + dlt + filled;
+                if (front_k > max_front) max_front = front_k;
+            } else if (phase1 && gleft == 0) {
+                // every pixel with g != 0 is filled: eq. ready from the next step on
+                phase1 = false;
+                data_switch = k + 1;
+                reval = true;
+            }
             int fk = filled;
             if (filled == 0) {
                 if (n_front + dlt == 0) break;  // Algorithm 1: D^(k) exhausted (or the rest unreachable)
@@ -1012,6 +1086,8 @@ __global__ void __launch_bounds__(fill_warps(RW) * 32, 1) fill_kernel(const __gr
             st.max_front = max_front;
             st.holes = holes;
             st.rechecks = __ldcg(&ctl->rechecks);
+            st.data_switch = data_switch;
+            st.reserved = 0;
             if (status == GF_OK && filled_tot < holes) status = GF_INCOMPLETE;
             st.status = status;
             *F.stats = st;

@@ -83,6 +83,7 @@ struct FrameDev {
     int32_t *holes;               // |D_h| (written by the init kernel)
     int32_t *init_list;           // tiles holding part of d_active D^(0)_h (written by the init kernel)
     int32_t *init_count;          // [0] tiles on init_list, [1] |d_active D^(0)_h|
+    int32_t *gleft;               // GF_FLAG_DATA: unfilled hole pixels with g != 0 (init kernel, then fills)
 };
 
 // Per-cluster control block (global memory).  Counters are indexed by the step
@@ -125,6 +126,7 @@ struct InitArgs {
     const FrameDev *frames;
     const int32_t *cta_offset;
     int32_t n_frames;
+    uint32_t flags;
 };
 
 // guide-field sampler

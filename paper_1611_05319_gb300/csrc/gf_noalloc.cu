@@ -45,7 +45,7 @@ constexpr int64_t NOALLOC_MAX_TILES = 66561;
 constexpr size_t up256(size_t v) { return (v + 255) / 256 * 256; }
 
 struct Layout {
-    size_t U, Q, F, S, L, holes, icnt, desc, order, cursor, ctaoff, ctl, lists, total;
+    size_t U, Q, F, S, L, holes, gleft, icnt, desc, order, cursor, ctaoff, ctl, lists, total;
 };
 
 // scratch layout of one frame with T tiles, filled by one cluster
@@ -59,6 +59,7 @@ constexpr Layout layout(int64_t T)
     l.S = p; p = up256(p + 4 * (size_t)T);
     l.L = p; p = up256(p + 4 * (size_t)T);
     l.holes = p; p = up256(p + 4);
+    l.gleft = p; p = up256(p + 4);
     l.icnt = p; p = up256(p + 8);
     l.desc = p; p = up256(p + sizeof(FrameDev));
     l.order = p; p = up256(p + 4);
@@ -188,6 +189,7 @@ extern "C" gf_status gf_fill_noalloc(const gf_frame *f, const gf_params *p, gf_s
     d.F = (TileF *)(A + l.F);
     d.sched = (int32_t *)(A + l.S);
     d.holes = (int32_t *)(A + l.holes);
+    d.gleft = (int32_t *)(A + l.gleft);
     d.init_list = (int32_t *)(A + l.L);
     d.init_count = (int32_t *)(A + l.icnt);
     static thread_local FrameChunk ch;
@@ -221,6 +223,7 @@ extern "C" gf_status gf_fill_noalloc(const gf_frame *f, const gf_params *p, gf_s
 
     // ---- clear what must start at zero (the array keeps the last call's contents)
     if (cudaMemsetAsync(A + l.holes, 0, 4, st) != cudaSuccess) return GF_ERR_CUDA;
+    if (cudaMemsetAsync(A + l.gleft, 0, 4, st) != cudaSuccess) return GF_ERR_CUDA;
     if (cudaMemsetAsync(A + l.icnt, 0, 8, st) != cudaSuccess) return GF_ERR_CUDA;
     if (cudaMemsetAsync(A + l.ctl, 0, sizeof(GroupCtl), st) != cudaSuccess) return GF_ERR_CUDA;
     if (f->out_stall && cudaMemsetAsync(f->out_stall, 0, 4 * (((size_t)f->H * f->W + 1 + 31) / 32), st) != cudaSuccess)
@@ -235,6 +238,7 @@ extern "C" gf_status gf_fill_noalloc(const gf_frame *f, const gf_params *p, gf_s
     ia.frames = fp.frames;
     ia.cta_offset = (const int32_t *)(A + l.ctaoff);
     ia.n_frames = 1;
+    ia.flags = p->flags;
     init_kernel<<<(unsigned)ch.cta[1], 256, 0, st>>>(ia);
     order_kernel<<<1, 256, 0, st>>>(fp.frames, 1, fp.frame_order, fp.frame_cursor);
     if (cudaGetLastError() != cudaSuccess) return GF_ERR_CUDA;

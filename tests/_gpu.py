@@ -36,7 +36,7 @@ def assert_parity(o, g, labels, atol=COLOUR_ATOL, check_enter=True):
     if check_enter:
         assert np.array_equal(o["enter"], g["enter"]), _diff(o["enter"], g["enter"])
     so, sg = o["stats"], g["stats"]
-    for k in ("shells", "stalls", "filled", "max_front"):
+    for k in ("shells", "stalls", "filled", "max_front", "data_switch"):
         assert so[k] == sg[k], (k, so[k], sg[k])
     assert sg["holes"] == int((labels == 1).sum())
     assert np.array_equal(o["stall_steps"].astype(bool), g["stall_steps"])

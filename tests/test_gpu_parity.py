@@ -375,3 +375,42 @@ def test_split_schedule_gives_identical_results():
             assert (a["shells"], a["filled"], a["status"]) == (b["shells"], b["filled"], b["status"])
     o = oracle_fill(*frames[8], eps=3.0, mu=10.0)
     assert np.array_equal(o["shell"], outs[1][0][8])
+
+
+def test_host_buffer_pipeline_many_frames_matches_device_path():
+    """The host-buffer call pipelines its frames over four chunks (frames dealt
+    round-robin); seven frames of different sizes, some with guide fields and some
+    with splines, must come back in order and equal the device-buffer fills."""
+    import torch
+
+    import paper_1611_05319_gb300 as gf
+    ctx = gf.context(0)
+    cases = [_case(40 + 6 * i, 56 + 2 * i, 400 + i) for i in range(7)]
+    dev = torch.device("cuda", 0)
+    # frames 1, 4 take their guide field from splines (a short diagonal polyline each)
+    spl = {}
+    for i in (1, 4):
+        H, W = cases[i][1].shape
+        pts = np.array([[2.0, 2.0], [W / 2.0, H / 2.0], [W - 3.0, H - 3.0]], np.float32)
+        spl[i] = (np.array([0, 3], np.int32), pts)
+    guides = []
+    for i, (im, lb, g) in enumerate(cases):
+        if i in spl:
+            guides.append(ctx.guidance(torch.from_numpy(lb).to(dev), spl[i][0], spl[i][1], 3.0).cpu().numpy())
+        else:
+            guides.append(g)
+    ref = ctx.fill_batched([torch.from_numpy(rgba(im)).to(dev) for im, _, _ in cases],
+                           [torch.from_numpy(lb).to(dev) for _, lb, _ in cases],
+                           [torch.from_numpy(np.ascontiguousarray(g, np.float32)).to(dev) for g in guides], mu=10.0)
+    torch.cuda.synchronize()
+    outs = [np.zeros(lb.shape + (4,), np.float32) for _, lb, _ in cases]
+    shells = [np.zeros(lb.shape, np.int32) for _, lb, _ in cases]
+    st = ctx.fill_batched_host([rgba(im) for im, _, _ in cases], [lb for _, lb, _ in cases],
+                               [None if i in spl else g for i, (_, _, g) in enumerate(cases)], outs, shells,
+                               splines=[spl.get(i) for i in range(7)], eta=3.0, mu=10.0)
+    for i, r in enumerate(ref):
+        sh = r.shell.cpu().numpy()
+        assert np.array_equal(shells[i], sh), i
+        assert np.array_equal(outs[i][sh >= 0], r.rgba.cpu().numpy()[sh >= 0]), i
+        rs = r.stats()
+        assert (st[i]["filled"], st[i]["shells"], st[i]["holes"]) == (rs["filled"], rs["shells"], rs["holes"]), i

@@ -445,3 +445,52 @@ def test_guidance_tie_lowest_index():
     pts = np.array([[5, 10], [25, 10], [25, 14], [5, 14]], np.float32)
     g = oracle.guidance(lab, off, pts, eta=3.0)
     assert np.allclose(g[12, 15], [math.exp(-4 / 18), 0.0], atol=1e-7)
+
+
+# ----------------------------------------------------------------------------
+# Data term (eq. ready2, Section 3.5 possible extensions)
+# ----------------------------------------------------------------------------
+def _mixed_hole(H=48, W=64, seed=5):
+    """A horizontal band with guidance along it (g != 0) joined to a square blob
+    with g = 0."""
+    rng = np.random.default_rng(seed)
+    hole = np.zeros((H, W), bool)
+    hole[20:27, 6:40] = True          # band
+    hole[12:36, 40:58] = True         # blob
+    g = np.zeros((H, W, 2), np.float32)
+    g[20:27, 6:40] = (1.0, 0.0)
+    lab = synth.labels_from(hole)
+    u = rng.uniform(0, 1, (H, W, 3))
+    return u, lab, g, hole
+
+
+def test_data_term_without_guidance_is_the_plain_fill():
+    u, lab, _, _ = _mixed_hole()
+    g0 = np.zeros(lab.shape + (2,), np.float32)
+    a = oracle.fill(u, lab, g0)
+    b = oracle.fill(u, lab, g0, data_term=True)
+    assert np.array_equal(a["shell"], b["shell"]) and np.array_equal(a["u"], b["u"])
+    assert b["stats"]["data_switch"] == 0 and a["stats"]["data_switch"] == -1
+
+
+def test_data_term_fills_guided_pixels_first():
+    u, lab, g, hole = _mixed_hole()
+    r = oracle.fill(u, lab, g, data_term=True)
+    ks = r["stats"]["data_switch"]
+    sh = r["shell"]
+    gnz = (g[..., 0] != 0) | (g[..., 1] != 0)
+    assert ks > 0
+    # phase 1: every pixel filled before the switch has g != 0
+    assert np.all(gnz[(sh >= 0) & (sh < ks)])
+    # the switch: either every guided pixel is filled, or phase 1 had nothing ready
+    guided_left = np.any(gnz & hole & ((sh < 0) | (sh >= ks)))
+    if guided_left:
+        plain = oracle.fill(u, lab, g)
+        assert not np.array_equal(plain["shell"], sh)
+    # a constant image stays constant under the data term as well
+    c = oracle.fill(np.full_like(u, 0.375), lab, g, data_term=True)
+    assert np.allclose(c["u"][hole], 0.375, atol=1e-12)
+    # eq. ready2 changes the order: the plain fill reaches blob pixels earlier
+    plain = oracle.fill(u, lab, g)
+    blob = hole & ~gnz
+    assert sh[blob].min() >= ks and plain["shell"][blob].min() < ks
