@@ -8,7 +8,10 @@ into ``liboracle.so`` beside it on first use, or by ``build()``.
 Functions follow the paper (arxiv 1611.05319):
   fill       Algorithm 1 with the rotated ghost-pixel ball, eq. weight,
              eq. bilinearDef, eqs. confidence / ready (smart order)
-  guidance   guide field from splines, Section 3.3
+  guidance   guide field from splines, Section 3.3 (optionally weighted by
+             each spline's coherence factor |g_Gamma|)
+  detect_splines   automatic spline detection, Section 3.3 (ring R, Canny on
+             an annulus, structure tensor eq. structureTensor, g_Gamma)
   alg_bytes  algorithmic bytes of a fill under Algorithm 1's per-step semantics
   frozen_fill / fill_backward   (see the adjoint section below)
 """
@@ -23,6 +26,7 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "guidefill_oracle.c")
 _SRC_ADJ = os.path.join(_HERE, "guidefill_oracle_adjoint.c")
+_SRC_SPL = os.path.join(_HERE, "guidefill_oracle_splines.c")
 _LIB = os.path.join(_HERE, "liboracle.so")
 
 GHOST = 1
@@ -41,8 +45,24 @@ class Stats(C.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
+class DetParams(C.Structure):
+    _fields_ = [("sigma", C.c_float), ("rho", C.c_float), ("ring_dist", C.c_int32), ("annulus", C.c_int32),
+                ("t_high", C.c_float), ("t_low", C.c_float), ("length", C.c_float), ("Lambda", C.c_float)]
+
+
+class DetDebug(C.Structure):
+    _fields_ = [("d_hole", C.c_void_p), ("d_all", C.c_void_p), ("edge_nms", C.c_void_p), ("edge", C.c_void_p),
+                ("us", C.c_void_p), ("T", C.c_void_p), ("J", C.c_void_p)]
+
+
+# defaults of the detection (sigma = 2, rho = 4 as in the example of Section 3.3.1;
+# Lambda = 1e-5 as in Section 3.3)
+DETECT_DEFAULTS = dict(sigma=2.0, rho=4.0, ring_dist=0, annulus=2, t_high=0.04, t_low=0.015, length=48.0,
+                       Lambda=1e-5)
+
+
 def build(force: bool = False) -> str:
-    srcs = [s for s in (_SRC, _SRC_ADJ) if os.path.exists(s)]
+    srcs = [s for s in (_SRC, _SRC_ADJ, _SRC_SPL) if os.path.exists(s)]
     newest = max(os.path.getmtime(s) for s in srcs)
     if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < newest:
         tmp = _LIB + f".tmp{os.getpid()}"
@@ -65,7 +85,12 @@ def lib():
         _lib.oracle_fill.argtypes = [C.c_int, C.c_int, C.c_int, P, P, P, C.c_double, C.c_double,
                                      C.c_double, C.c_uint, C.c_float, C.c_int, P, P, P, P]
         _lib.oracle_guidance.restype = C.c_int
-        _lib.oracle_guidance.argtypes = [C.c_int, C.c_int, P, C.c_int, P, P, C.c_float, P]
+        _lib.oracle_guidance.argtypes = [C.c_int, C.c_int, P, C.c_int, P, P, C.c_float, P, P]
+        _lib.oracle_detect_splines.restype = C.c_int
+        _lib.oracle_detect_splines.argtypes = [C.c_int, C.c_int, P, P, C.POINTER(DetParams), C.c_int, P, P, P,
+                                               C.POINTER(DetDebug)]
+        _lib.oracle_gauss_taps.restype = C.c_int
+        _lib.oracle_gauss_taps.argtypes = [C.c_float, P]
         _lib.oracle_alg_bytes.restype = C.c_int64
         _lib.oracle_alg_bytes.argtypes = [C.c_int, C.c_int, P, P, C.c_double, C.c_uint, C.c_float,
                                           P, P]
@@ -115,15 +140,18 @@ def fill(rgb, labels, guide, eps=3.0, mu=50.0, c=0.05, ghost=True, smart=True, t
                 status=rc)
 
 
-def guidance(labels, offsets, pts, eta=3.0, H=None, W=None):
+def guidance(labels, offsets, pts, eta=3.0, H=None, W=None, weight=None):
     """Guide field from polylines (Section 3.3), float32 [H, W, 2]; zero outside
-    the hole."""
+    the hole.  weight: optional float32 [n_splines], the magnitude |g_Gamma| of
+    each spline's direction (1 when omitted)."""
     lab = np.ascontiguousarray(labels, np.uint8)
     H, W = lab.shape
     off = np.ascontiguousarray(offsets, np.int32)
     P = np.ascontiguousarray(pts, np.float32)
     g = np.zeros((H, W, 2), np.float32)
-    rc = lib().oracle_guidance(H, W, _p(lab), len(off) - 1, _p(off), _p(P), _f32(eta), _p(g))
+    w = None if weight is None else np.ascontiguousarray(weight, np.float32)
+    assert w is None or w.shape == (len(off) - 1,)
+    rc = lib().oracle_guidance(H, W, _p(lab), len(off) - 1, _p(off), _p(P), _f32(eta), _p(w), _p(g))
     if rc != 0:
         raise ValueError("oracle_guidance: bad arguments")
     return g
@@ -183,3 +211,46 @@ def fill_backward(u_out, labels, guide, shell, stall_steps, grad_out, eps=3.0, m
     lib().oracle_fill_backward(H, W, Cn, _p(u), _p(lab), _p(g), _f32(eps), float(mu), _f32(tau), _p(sh),
                                _p(_stall_u8(stall_steps, K)), K, _p(go), _p(gi), _p(gphi), C.byref(gmu))
     return gi, gphi, gmu.value
+
+
+def gauss_taps(s):
+    """The normalised FP32 taps of g_s the detection uses (radius ceil(2 s))."""
+    w = np.zeros(129, np.float32)
+    r = lib().oracle_gauss_taps(_f32(s), _p(w))
+    return w[:2 * r + 1].copy()
+
+
+def detect_splines(rgb, labels, max_splines=4096, debug=False, **kw):
+    """Automatic spline detection of Section 3.3 on an RGB(A) image (float32
+    [H, W, >=3]; the first three channels are used) with labels (0 known, 1
+    hole, 2 bystander).  Returns dict(count, pts [n, 2, 2] (base, end), weight
+    [n], base [n] (pixel index y W + x)) for the first n = min(count,
+    max_splines) splines in raster order of their base; with debug=True also
+    the per-pixel maps d_hole, d_all, edge_nms, edge, us, T, J."""
+    prm = dict(DETECT_DEFAULTS)
+    prm.update(kw)
+    lab = np.ascontiguousarray(labels, np.uint8)
+    H, W = lab.shape
+    rgb3 = np.ascontiguousarray(np.asarray(rgb)[..., :3], np.float32)
+    assert rgb3.shape == (H, W, 3)
+    P = DetParams(_f32(prm["sigma"]), _f32(prm["rho"]), int(prm["ring_dist"]), int(prm["annulus"]),
+                  _f32(prm["t_high"]), _f32(prm["t_low"]), _f32(prm["length"]), _f32(prm["Lambda"]))
+    pts = np.zeros((max(max_splines, 1), 2, 2), np.float32)
+    wt = np.zeros(max(max_splines, 1), np.float32)
+    base = np.zeros(max(max_splines, 1), np.int32)
+    maps = {}
+    dbg = None
+    if debug:
+        maps = dict(d_hole=np.zeros((H, W), np.int32), d_all=np.zeros((H, W), np.int32),
+                    edge_nms=np.zeros((H, W), np.uint8), edge=np.zeros((H, W), np.uint8),
+                    us=np.zeros((H, W, 3), np.float32), T=np.zeros((H, W, 3), np.float32),
+                    J=np.zeros((H, W, 3), np.float32))
+        dbg = DetDebug(*[_p(maps[k]) for k, _ in DetDebug._fields_])
+    rc = lib().oracle_detect_splines(H, W, _p(rgb3), _p(lab), C.byref(P), int(max_splines), _p(pts), _p(wt),
+                                     _p(base), C.byref(dbg) if dbg is not None else None)
+    if rc < 0:
+        raise ValueError("oracle_detect_splines: bad arguments")
+    n = min(rc, max_splines)
+    out = dict(count=rc, pts=pts[:n].copy(), weight=wt[:n].copy(), base=base[:n].copy())
+    out.update(maps)
+    return out

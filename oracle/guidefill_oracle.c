@@ -437,7 +437,7 @@ static float seg_dist2_f32(float px, float py, float ax, float ay, float bx, flo
 }
 
 int oracle_guidance(int H, int W, const uint8_t *lab, int n_splines, const int32_t *offsets,
-                    const float *pts, float eta, float *guide)
+                    const float *pts, float eta, const float *weight, float *guide)
 {
     if (H <= 0 || W <= 0 || n_splines < 0 || !(eta > 0.0f)) return -1;
     float t3 = 3.0f * eta;
@@ -470,8 +470,14 @@ int oracle_guidance(int H, int W, const uint8_t *lab, int n_splines, const int32
                 continue;
             }
             /* FP64 value for the chosen segment: t = ((x - a).v) * (1/|v|^2) clamped to
-             * [0, 1], d^2 = |x - a - t v|^2, g = (v/|v|) * exp(-(d^2 * (1/(2 eta^2)))),
-             * rounded once to FP32 (Section 3.3). */
+             * [0, 1], d^2 = |x - a - t v|^2, g = (v/|v|) * exp(-(d^2 * (1/(2 eta^2)))) * w,
+             * rounded once to FP32 (Section 3.3: g_Gamma e^(-d^2/(2 eta^2)) with
+             * |g_Gamma| = w the spline's coherence weight). */
+            /* the spline holding segment bi, for its weight (the coherence factor of
+             * g_Gamma; 1 when no weights are given) */
+            int sb = 0;
+            while (offsets[sb + 1] <= bi) sb++;
+            double w = weight ? (double)weight[sb] : 1.0;
             double ax = pts[2 * bi], ay = pts[2 * bi + 1];
             double bx = pts[2 * bi + 2], by = pts[2 * bi + 3];
             double vx = bx - ax, vy = by - ay;
@@ -484,8 +490,8 @@ int oracle_guidance(int H, int W, const uint8_t *lab, int n_splines, const int32
             double qx = wx - t * vx, qy = wy - t * vy;
             double d2 = qx * qx + qy * qy;
             double e = exp(-(d2 * k2));
-            guide[2 * p] = (float)(vx / len * e);
-            guide[2 * p + 1] = (float)(vy / len * e);
+            guide[2 * p] = (float)(vx / len * e * w);
+            guide[2 * p + 1] = (float)(vy / len * e * w);
         }
     return 0;
 }
