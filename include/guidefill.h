@@ -215,12 +215,81 @@ typedef struct {
     const int32_t *offsets; /* device [n_splines+1] */
     const float *pts;       /* device [n_points][2] */
     float *guide;           /* device [H][W][2] */
+    const float *weight;    /* device [n_splines] or NULL: |g_Gamma| of each spline (Section 3.3), the
+                               factor the spline's field is multiplied by (in FP64, before the one
+                               rounding); NULL = 1 */
 } gf_spline_frame;
 
 /* gf_guidance_from_splines for n frames in one launch sequence; frames is a
  * HOST array. */
 gf_status gf_guidance_batched(gf_ctx *ctx, int n, const gf_spline_frame *frames, float eta,
                               void *stream);
+
+/*
+ * Automatic spline detection (Section 3.3).  A ring R of known pixels at
+ * Chebyshev distance ring_dist from the hole D_h (labels == 1), with no hole or
+ * bystander pixel nearer; Canny edge detection on the annulus of known pixels
+ * within `annulus` of that distance; and for every ring pixel on an accepted
+ * edge a straight spline of length `length` from the pixel along the minor
+ * eigenvector v- of the structure tensor J_{sigma,rho} (eq. structureTensor) at
+ * that pixel, signed to point into D_h, with the weight tanh((lambda+ -
+ * lambda-)/Lambda) of g_Gamma.  Definitions, all in FP32 with no contraction
+ * unless stated:
+ *  - u_sigma = g_sigma * u per colour channel (R, G, B; alpha unused); g_s has
+ *    radius ceil(2 s) (window 4 s + 1), taps exp(-i^2/(2 s^2)) (FP64, rounded)
+ *    divided by their FP32 sum, applied along rows then columns, taps in order
+ *    -r..r, image coordinates clamped;
+ *  - gradient by central differences (one-sided at the border); T = sum over
+ *    channels of grad u_sigma (x) grad u_sigma; J = g_rho * T (same blur);
+ *  - Canny: m2 = Txx + Tyy; direction from d = Txx - Tyy, e = 2 Txy quantised
+ *    to 0/45/90/135 degrees (|e| <= d: 0; |e| <= -d: 90; e > 0: 45; else 135);
+ *    kept by suppression when m2 >= m2 of both neighbours along it; strong when
+ *    m2 > t_high^2, weak when m2 > t_low^2; weak pixels kept when 8-connected
+ *    through kept annulus pixels to a strong one;
+ *  - eigenvectors: r = sqrt(d^2 + e^2) = lambda+ - lambda- of J; v+ ~ (d + r, e)
+ *    if d >= 0 else (e, r - d) ((1, 0) if both vanish), normalised, v- =
+ *    (-v+_y, v+_x);
+ *  - sign: -v- when the hole distance at base - ring_dist v- (rounded to the
+ *    nearest pixel, clamped) is smaller than at base + ring_dist v-, else +v-;
+ *  - weight = tanh(r / Lambda) in FP64, rounded.
+ * Every set (ring, annulus, edges, splines) and every spline end point is
+ * therefore decided by correctly rounded operations only.
+ */
+typedef struct {
+    float sigma, rho;   /* Gaussian scales of J_{sigma,rho}; 0 < sigma <= 4, 0 < rho <= 8 */
+    int32_t ring_dist;  /* dR >= 1; 0 = ceil(2 sigma) + ceil(2 rho) + 2, the smallest distance at
+                           which the tensor's windows and the gradient stencil miss D_h u B_h */
+    int32_t annulus;    /* 0 <= annulus <= 16, annulus < dR; ring_dist + annulus <= 96 */
+    float t_high, t_low; /* Canny thresholds on |grad u_sigma| (channels in quadrature) */
+    float length;       /* spline length in pixels, > 0 */
+    float Lambda;       /* > 0; Section 3.3 default 1e-5 */
+} gf_detect_params;
+
+/* One frame of a detection request (all DEVICE pointers). */
+typedef struct {
+    int32_t H, W;
+    const float *rgba;      /* [H][W][4] */
+    const uint8_t *labels;  /* [H][W] */
+    int32_t max_splines;    /* capacity of the outputs below, >= 0 */
+    float *pts;             /* [max_splines][2][2]: base (x, y), end (x, y); 8-byte aligned */
+    float *weight;          /* [max_splines] */
+    int32_t *offsets;       /* [max_splines + 1]: offsets[s] = 2 min(s, n), so (pts, offsets) with
+                               n_splines = max_splines, n_points = 2 max_splines is a valid input of
+                               gf_guidance_batched whatever n is */
+    int32_t *base;          /* [max_splines] or NULL: pixel index y W + x of each spline's base */
+    uint8_t *edges;         /* [H][W] or NULL: 1 where the annulus holds an accepted edge, else 0 */
+    int32_t *result;        /* [2]: result[0] = n, the number of splines found (the first
+                               min(n, max_splines) in raster order of their base are written);
+                               result[1] = 0, or GF_ERR_TIMEOUT if a bounded device loop gave up */
+} gf_detect_frame;
+
+/* Detection for n frames in one launch sequence (frames: HOST array).  Scratch
+ * is about 28 bytes per pixel, owned by the context.  GF_ERR_ARG when a
+ * parameter is out of the ranges above or a pointer is missing or misaligned. */
+gf_status gf_detect_splines_batched(gf_ctx *ctx, int n, const gf_detect_frame *frames,
+                                    const gf_detect_params *params, void *stream);
+gf_status gf_detect_splines(gf_ctx *ctx, const gf_detect_frame *frame, const gf_detect_params *params,
+                            void *stream);
 
 /*
  * Guide field from an angle field: g = mag * (cos phi, sin phi) at hole pixels

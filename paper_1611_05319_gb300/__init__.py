@@ -20,8 +20,8 @@ import torch
 from . import _lib
 from ._lib import STATS_BYTES, STATS_DTYPE, GuidefillError, check, lib, make_params
 
-__all__ = ["Context", "context", "fill", "fill_batched", "guidance", "FillResult", "GuidefillError",
-           "to_rgba", "STATS_DTYPE"]
+__all__ = ["Context", "context", "fill", "fill_batched", "guidance", "detect_splines", "guidance_auto",
+           "FillResult", "DetectResult", "GuidefillError", "to_rgba", "STATS_DTYPE"]
 
 
 def _ptr(t: Optional[torch.Tensor]):
@@ -63,6 +63,33 @@ class FillResult:
         bits = self.stall.cpu().numpy().view(np.uint32)
         idx = np.arange(K)
         return ((bits[idx >> 5] >> (idx & 31)) & 1).astype(bool)
+
+
+@dataclass
+class DetectResult:
+    """Splines of one frame from gf_detect_splines (device tensors): pts
+    [max_splines, 2, 2] (base, end), weight [max_splines] (|g_Gamma|), offsets
+    [max_splines + 1] (polyline offsets 2 min(s, n)), base [max_splines] (pixel
+    index of each base), result [2] (n found, status), edges [H, W] or None."""
+    pts: torch.Tensor
+    weight: torch.Tensor
+    offsets: torch.Tensor
+    base: torch.Tensor
+    result: torch.Tensor
+    edges: Optional[torch.Tensor]
+    max_splines: int
+
+    def count(self) -> int:
+        """Synchronises; the number of splines found (may exceed max_splines)."""
+        r = self.result.cpu().tolist()
+        if r[1] != 0:
+            raise GuidefillError(r[1], "gf_detect_splines (device)")
+        return int(r[0])
+
+    def splines(self):
+        """Synchronises; (pts [n, 2, 2], weight [n], base [n]) as numpy for the n written."""
+        n = min(self.count(), self.max_splines)
+        return (self.pts[:n].cpu().numpy(), self.weight[:n].cpu().numpy(), self.base[:n].cpu().numpy())
 
 
 class Context:
@@ -226,12 +253,14 @@ class Context:
         return g
 
     # -------------------------------------------------------------- guidance
-    def guidance(self, labels, offsets, pts, eta=3.0, out=None, stream=None) -> torch.Tensor:
+    def guidance(self, labels, offsets, pts, eta=3.0, out=None, stream=None, weight=None) -> torch.Tensor:
         """Guide field from polylines (Section 3.3), written at hole pixels of ``out``
-        (zero-initialised [H,W,2] float32 when not given)."""
-        return self.guidance_batched([labels], [offsets], [pts], eta, None if out is None else [out], stream)[0]
+        (zero-initialised [H,W,2] float32 when not given); ``weight`` [n_splines]
+        scales each spline's field (|g_Gamma|, 1 when omitted)."""
+        return self.guidance_batched([labels], [offsets], [pts], eta, None if out is None else [out], stream,
+                                     None if weight is None else [weight])[0]
 
-    def guidance_batched(self, labels, offsets, pts, eta=3.0, out=None, stream=None):
+    def guidance_batched(self, labels, offsets, pts, eta=3.0, out=None, stream=None, weight=None):
         dev = torch.device("cuda", self.device)
         n = len(labels)
         frames = (_lib.SplineFrame * n)()
@@ -242,15 +271,81 @@ class Context:
             P = torch.as_tensor(pts[i], dtype=torch.float32).to(dev).contiguous()
             H, W = lab.shape
             g = out[i] if out is not None else torch.zeros((H, W, 2), dtype=torch.float32, device=dev)
-            frames[i] = _lib.SplineFrame(H, W, lab.data_ptr(), off.numel() - 1, P.shape[0], off.data_ptr(),
-                                         P.data_ptr(), g.data_ptr())
+            w = None
+            if weight is not None and weight[i] is not None:
+                w = torch.as_tensor(weight[i], dtype=torch.float32).to(dev).contiguous()
+                if w.numel() != off.numel() - 1:
+                    raise ValueError("weight needs one value per spline")
+            frames[i] = _lib.SplineFrame(H, W, lab.data_ptr(), off.numel() - 1, P.reshape(-1, 2).shape[0],
+                                         off.data_ptr(), P.data_ptr(), g.data_ptr(), _ptr(w))
             outs.append(g)
-            keep.append((lab, off, P))
+            keep.append((lab, off, P, w))
         with torch.cuda.device(self.device):
             check(lib().gf_guidance_batched(self._h, n, frames, C.c_float(eta), _stream(stream)),
                   "gf_guidance_batched", self._h)
         self._gkeep = keep
         return outs
+
+    # ----------------------------------------------------- spline detection
+    def detect_splines_batched(self, rgba: Sequence[torch.Tensor], labels: Sequence[torch.Tensor], max_splines=4096,
+                               edges=False, stream=None, **params) -> List[DetectResult]:
+        """Automatic spline detection (Section 3.3) on device frames: rgba [H,W,4]
+        (or [H,W,3]) float32, labels [H,W] uint8.  ``params``: sigma, rho,
+        ring_dist, annulus, t_high, t_low, length, Lambda (see ``_lib.DETECT_DEFAULTS``).
+        Results stay on the device; ``count`` is a device int32 tensor [2]
+        (number found, status)."""
+        dev = torch.device("cuda", self.device)
+        n = len(rgba)
+        frames = (_lib.DetectFrame * n)()
+        outs, keep = [], []
+        for i in range(n):
+            img = to_rgba(rgba[i].to(dev, torch.float32))
+            lab = labels[i].to(dev, torch.uint8).contiguous()
+            H, W = lab.shape
+            m = int(max_splines)
+            pts = torch.zeros((max(m, 1), 2, 2), dtype=torch.float32, device=dev)
+            wt = torch.zeros((max(m, 1),), dtype=torch.float32, device=dev)
+            off = torch.zeros((m + 1,), dtype=torch.int32, device=dev)
+            base = torch.zeros((max(m, 1),), dtype=torch.int32, device=dev)
+            res = torch.zeros((2,), dtype=torch.int32, device=dev)
+            ed = torch.zeros((H, W), dtype=torch.uint8, device=dev) if edges else None
+            frames[i] = _lib.DetectFrame(H, W, img.data_ptr(), lab.data_ptr(), m, pts.data_ptr(), wt.data_ptr(),
+                                         off.data_ptr(), base.data_ptr(), _ptr(ed), res.data_ptr())
+            outs.append(DetectResult(pts, wt, off, base, res, ed, m))
+            keep.append((img, lab))
+        prm = _lib.make_detect_params(**params)
+        with torch.cuda.device(self.device):
+            check(lib().gf_detect_splines_batched(self._h, n, frames, C.byref(prm), _stream(stream)),
+                  "gf_detect_splines_batched", self._h)
+        self._dkeep = keep
+        return outs
+
+    def detect_splines(self, rgba, labels, **kw) -> "DetectResult":
+        return self.detect_splines_batched([rgba], [labels], **kw)[0]
+
+    def guidance_auto_batched(self, rgba, labels, eta=3.0, max_splines=4096, out=None, stream=None, **params):
+        """Detected splines (Section 3.3) straight into the guide field, with no
+        host synchronisation: each frame's guide field comes from its detected
+        splines weighted by their coherence factor.  Returns (guides, detections)."""
+        det = self.detect_splines_batched(rgba, labels, max_splines=max_splines, stream=stream, **params)
+        dev = torch.device("cuda", self.device)
+        n = len(rgba)
+        frames = (_lib.SplineFrame * n)()
+        outs, keep = [], []
+        for i in range(n):
+            lab = labels[i].to(dev, torch.uint8).contiguous()
+            H, W = lab.shape
+            g = out[i] if out is not None else torch.zeros((H, W, 2), dtype=torch.float32, device=dev)
+            d = det[i]
+            frames[i] = _lib.SplineFrame(H, W, lab.data_ptr(), d.max_splines, 2 * d.max_splines, d.offsets.data_ptr(),
+                                         d.pts.data_ptr(), g.data_ptr(), d.weight.data_ptr())
+            outs.append(g)
+            keep.append(lab)
+        with torch.cuda.device(self.device):
+            check(lib().gf_guidance_batched(self._h, n, frames, C.c_float(eta), _stream(stream)),
+                  "gf_guidance_batched", self._h)
+        self._gkeep = keep
+        return outs, det
 
     # ---------------------------------------------------- host-buffer path
     def fill_batched_host(self, rgba: Sequence[np.ndarray], labels: Sequence[np.ndarray],
@@ -316,3 +411,14 @@ def fill_batched(rgba, labels, guide, **kw) -> List[FillResult]:
 
 def guidance(labels, offsets, pts, eta=3.0, **kw) -> torch.Tensor:
     return context().guidance(labels, offsets, pts, eta, **kw)
+
+
+def detect_splines(rgba, labels, **kw) -> DetectResult:
+    return context(rgba.device.index if rgba.is_cuda else None).detect_splines(rgba, labels, **kw)
+
+
+def guidance_auto(rgba, labels, eta=3.0, **kw):
+    """Guide field from automatically detected splines; returns (guide, detection)."""
+    ctx = context(rgba.device.index if rgba.is_cuda else None)
+    g, d = ctx.guidance_auto_batched([rgba], [labels], eta, **kw)
+    return g[0], d[0]

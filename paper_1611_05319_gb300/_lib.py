@@ -26,7 +26,8 @@ STATUS = {0: "ok", 1: "incomplete", -1: "invalid argument", -2: "CUDA error", -3
 EXPORTS = ["gf_create", "gf_destroy", "gf_status_string", "gf_last_cuda_error", "gf_fill",
            "gf_fill_batched", "gf_fill_batched_ex", "gf_fill_batched_host", "gf_guidance_from_splines", "gf_guidance_batched",
            "gf_set_launch_config", "gf_get_last_launch", "gf_max_active_clusters", "gf_fill_backward",
-           "gf_guide_from_angle", "gf_autotune", "gf_fill_noalloc", "gf_set_split", "gf_get_last_split"]
+           "gf_guide_from_angle", "gf_autotune", "gf_fill_noalloc", "gf_set_split", "gf_get_last_split",
+           "gf_detect_splines", "gf_detect_splines_batched"]
 
 
 class Frame(C.Structure):
@@ -42,7 +43,19 @@ class Params(C.Structure):
 
 class SplineFrame(C.Structure):
     _fields_ = [("H", C.c_int32), ("W", C.c_int32), ("labels", C.c_void_p), ("n_splines", C.c_int32),
-                ("n_points", C.c_int32), ("offsets", C.c_void_p), ("pts", C.c_void_p), ("guide", C.c_void_p)]
+                ("n_points", C.c_int32), ("offsets", C.c_void_p), ("pts", C.c_void_p), ("guide", C.c_void_p),
+                ("weight", C.c_void_p)]
+
+
+class DetectParams(C.Structure):
+    _fields_ = [("sigma", C.c_float), ("rho", C.c_float), ("ring_dist", C.c_int32), ("annulus", C.c_int32),
+                ("t_high", C.c_float), ("t_low", C.c_float), ("length", C.c_float), ("Lambda", C.c_float)]
+
+
+class DetectFrame(C.Structure):
+    _fields_ = [("H", C.c_int32), ("W", C.c_int32), ("rgba", C.c_void_p), ("labels", C.c_void_p),
+                ("max_splines", C.c_int32), ("pts", C.c_void_p), ("weight", C.c_void_p), ("offsets", C.c_void_p),
+                ("base", C.c_void_p), ("edges", C.c_void_p), ("result", C.c_void_p)]
 
 
 class AdjointFrame(C.Structure):
@@ -114,6 +127,10 @@ def lib() -> C.CDLL:
         L.gf_set_split.restype = C.c_int
         L.gf_get_last_split.argtypes = [P, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int)]
         L.gf_get_last_split.restype = C.c_int
+        L.gf_detect_splines.argtypes = [P, C.POINTER(DetectFrame), C.POINTER(DetectParams), P]
+        L.gf_detect_splines.restype = C.c_int
+        L.gf_detect_splines_batched.argtypes = [P, C.c_int, C.POINTER(DetectFrame), C.POINTER(DetectParams), P]
+        L.gf_detect_splines_batched.restype = C.c_int
         _lib = L
     return _lib
 
@@ -132,3 +149,19 @@ def make_params(eps=3.0, mu=50.0, c=0.05, ghost=True, smart=True, rescan=False, 
     flags = (GF_FLAG_GHOST if ghost else 0) | (GF_FLAG_SMART if smart else 0) | (GF_FLAG_RESCAN if rescan else 0) | \
         (GF_FLAG_DATA if data_term else 0)
     return Params(float(eps), float(mu), float(c), flags, float(snap_tau), int(max_shells))
+
+
+# Section 3.3's example values sigma = 2, rho = 4 and Lambda = 1e-5; thresholds on
+# |grad u_sigma| for colours in [0, 1]
+DETECT_DEFAULTS = dict(sigma=2.0, rho=4.0, ring_dist=0, annulus=2, t_high=0.04, t_low=0.015, length=48.0,
+                       Lambda=1e-5)
+
+
+def make_detect_params(**kw):
+    d = dict(DETECT_DEFAULTS)
+    unknown = set(kw) - set(d)
+    if unknown:
+        raise TypeError(f"unknown detection parameters: {sorted(unknown)}")
+    d.update(kw)
+    return DetectParams(float(d["sigma"]), float(d["rho"]), int(d["ring_dist"]), int(d["annulus"]),
+                        float(d["t_high"]), float(d["t_low"]), float(d["length"]), float(d["Lambda"]))

@@ -8,7 +8,7 @@
 #include <cstring>
 #include <vector>
 
-#include "gf_internal.cuh"
+#include "gf_detect.cuh"
 
 
 using namespace gf;
@@ -26,6 +26,7 @@ struct gf_ctx {
     DevBuf garena;      // guidance scratch
     DevBuf io;          // host-buffer path device copies
     DevBuf aarena;      // adjoint scratch
+    DevBuf darena;      // spline-detection scratch
     // cached graphs of the last batched fill: gexec = preparation (descriptor
     // upload, clears, init, frame order), gexec_fill = the persistent fill kernel
     cudaGraphExec_t gexec = nullptr;
@@ -293,6 +294,7 @@ void gf_destroy(gf_ctx *ctx)
     if (ctx->garena.ptr) cudaFree(ctx->garena.ptr);
     if (ctx->io.ptr) cudaFree(ctx->io.ptr);
     if (ctx->aarena.ptr) cudaFree(ctx->aarena.ptr);
+    if (ctx->darena.ptr) cudaFree(ctx->darena.ptr);
     delete ctx;
 }
 
@@ -883,6 +885,19 @@ gf_status gf_guidance_batched(gf_ctx *ctx, int n, const gf_spline_frame *frames,
     if (pp > 0) {
         bin_kernel<<<(unsigned)((pp + 255) / 256), 256, 0, st>>>(ga, (int)pp);
         CK(cudaGetLastError());
+        for (int c0 = 0; c0 < n; c0 += DESC_CHUNK) {
+            WeightChunk wc;
+            wc.first = c0;
+            wc.count = std::min(DESC_CHUNK, n - c0);
+            bool any = false;
+            for (int i = 0; i < wc.count; i++) {
+                wc.w[i] = frames[c0 + i].n_points > 1 ? frames[c0 + i].weight : nullptr;
+                any = any || wc.w[i];
+            }
+            if (!any) continue;
+            spline_weight_kernel<<<(unsigned)wc.count, 256, 0, st>>>(ga, wc);
+            CK(cudaGetLastError());
+        }
     }
     guide_kernel<<<(unsigned)bb, 256, 0, st>>>(ga);
     CK(cudaGetLastError());
@@ -895,8 +910,151 @@ gf_status gf_guidance_from_splines(gf_ctx *ctx, int H, int W, const uint8_t *lab
 {
     gf_spline_frame f;
     f.H = H; f.W = W; f.labels = labels; f.n_splines = n_splines; f.n_points = n_points;
+    f.weight = nullptr;
     f.offsets = offsets; f.pts = pts; f.guide = guide;
     return gf_guidance_batched(ctx, 1, &f, eta, stream);
+}
+
+// Normalised taps of g_s (radius ceil(2 s)): exp(-i^2/(2 s^2)) in FP64 rounded
+// to FP32, divided by their FP32 sum (Section 3.3's (4 s + 1) windows).
+static int gauss_taps(float s, float *w)
+{
+    const int r = (int)std::ceil(2.0 * (double)s);
+    float sum = 0.0f;
+    for (int i = -r; i <= r; i++) {
+        w[i + r] = (float)std::exp(-(double)(i * i) / (2.0 * (double)s * (double)s));
+        sum = sum + w[i + r];
+    }
+    for (int i = 0; i <= 2 * r; i++) w[i] = w[i] / sum;
+    return r;
+}
+
+gf_status gf_detect_splines_batched(gf_ctx *ctx, int n, const gf_detect_frame *frames, const gf_detect_params *prm,
+                                    void *stream)
+{
+    if (!ctx || n <= 0 || !frames || !prm) return GF_ERR_ARG;
+    const gf_detect_params P = *prm;
+    if (!(P.sigma > 0.0f && P.sigma <= 4.0f) || !(P.rho > 0.0f && P.rho <= 8.0f)) return GF_ERR_ARG;
+    if (!(P.t_high >= 0.0f) || !(P.t_low >= 0.0f) || !std::isfinite(P.t_high) || !std::isfinite(P.t_low))
+        return GF_ERR_ARG;
+    if (!(P.length > 0.0f) || !std::isfinite(P.length) || !(P.Lambda > 0.0f) || !std::isfinite(P.Lambda))
+        return GF_ERR_ARG;
+    const int rS = (int)std::ceil(2.0 * (double)P.sigma), rR = (int)std::ceil(2.0 * (double)P.rho);
+    const int dR = P.ring_dist > 0 ? P.ring_dist : rS + rR + 2;
+    if (P.ring_dist < 0 || P.annulus < 0 || P.annulus > 16 || P.annulus >= dR || dR + P.annulus > 96)
+        return GF_ERR_ARG;
+    for (int i = 0; i < n; i++) {
+        const gf_detect_frame &f = frames[i];
+        if (f.H <= 0 || f.W <= 0 || !f.rgba || !f.labels || !f.result || !f.offsets || f.max_splines < 0)
+            return GF_ERR_ARG;
+        if ((int64_t)f.H * f.W > ((int64_t)1 << 31) - 64) return GF_ERR_ARG;
+        if (f.max_splines > 0 && (!f.pts || !f.weight)) return GF_ERR_ARG;
+        if (((uintptr_t)f.rgba & 15) || (f.pts && ((uintptr_t)f.pts & 7)) || ((uintptr_t)f.result & 3) ||
+            ((uintptr_t)f.offsets & 3) || (f.weight && ((uintptr_t)f.weight & 3)) || (f.base && ((uintptr_t)f.base & 3)))
+            return GF_ERR_ARG;
+    }
+    cudaError_t e = cudaSetDevice(ctx->device);
+    if (e != cudaSuccess) return cuda_fail(ctx, e);
+    cudaStream_t st = (cudaStream_t)stream;
+    // scratch per frame: distances, tile flags, edge classes, union-find, candidates, row-segment masks
+    std::vector<DetectFrameDev> hd(n);
+    std::vector<int32_t> hto(n + 1);
+    std::vector<size_t> o_dist(n), o_act(n), o_edge(n), o_par(n), o_mark(n), o_cand(n), o_accm(n), o_accp(n);
+    size_t pos = 0;
+    int64_t tiles = 0;
+    for (int i = 0; i < n; i++) {
+        const size_t np = (size_t)frames[i].H * frames[i].W;
+        const int NBX = (frames[i].W + DT - 1) / DT, NBY = (frames[i].H + DT - 1) / DT;
+        o_dist[i] = pos; pos = align_up(pos + 2 * np, 256);
+        o_act[i] = pos; pos = align_up(pos + (size_t)NBX * NBY, 256);
+        o_edge[i] = pos; pos = align_up(pos + np, 256);
+        o_par[i] = pos; pos = align_up(pos + 4 * np, 256);
+        o_mark[i] = pos; pos = align_up(pos + 4 * np, 256);
+        o_cand[i] = pos; pos = align_up(pos + 16 * np, 256);
+        o_accm[i] = pos; pos = align_up(pos + 4 * (size_t)frames[i].H * NBX, 256);
+        o_accp[i] = pos; pos = align_up(pos + 4 * (size_t)frames[i].H * NBX, 256);
+        hto[i] = (int32_t)tiles;
+        tiles += (int64_t)NBX * NBY;
+    }
+    hto[n] = (int32_t)tiles;
+    if (tiles >= INT32_MAX) return GF_ERR_ARG;
+    const size_t o_desc = pos; pos = align_up(pos + sizeof(DetectFrameDev) * (size_t)n, 256);
+    const size_t o_to = pos; pos = align_up(pos + 4 * (size_t)(n + 1), 256);
+    gf_status s = ensure(ctx, ctx->darena, pos);
+    if (s != GF_OK) return s;
+    char *A = (char *)ctx->darena.ptr;
+    for (int i = 0; i < n; i++) {
+        const gf_detect_frame &f = frames[i];
+        DetectFrameDev d;
+        d.H = f.H; d.W = f.W;
+        d.NBX = (f.W + DT - 1) / DT; d.NBY = (f.H + DT - 1) / DT;
+        d.rgba = (const float4 *)f.rgba; d.labels = f.labels;
+        d.dist = (uchar2 *)(A + o_dist[i]);
+        d.active = (uint8_t *)(A + o_act[i]);
+        d.edge = (uint8_t *)(A + o_edge[i]);
+        d.parent = (int32_t *)(A + o_par[i]);
+        d.mark = (int32_t *)(A + o_mark[i]);
+        d.cand = (float4 *)(A + o_cand[i]);
+        d.accm = (uint32_t *)(A + o_accm[i]);
+        d.accpos = (uint32_t *)(A + o_accp[i]);
+        d.pts = (float2 *)f.pts; d.weight = f.weight; d.offsets = f.offsets; d.base = f.base;
+        d.edges_out = f.edges; d.result = f.result;
+        d.max_splines = f.max_splines; d.pad = 0;
+        hd[i] = d;
+    }
+    for (int c0 = 0; c0 < n; c0 += DET_CHUNK) {
+        static thread_local DetectChunk ch;
+        ch.dst_frames = (DetectFrameDev *)(A + o_desc);
+        ch.dst_to = (int32_t *)(A + o_to);
+        ch.first = c0;
+        ch.count = std::min(DET_CHUNK, n - c0);
+        ch.last_chunk = (c0 + ch.count == n) ? 1 : 0;
+        for (int i = 0; i < ch.count; i++) {
+            ch.frames[i] = hd[c0 + i];
+            ch.to[i] = hto[c0 + i];
+        }
+        ch.to[ch.count] = hto[c0 + ch.count];
+        upload_detect_kernel<<<1, 64, 0, st>>>(ch);
+        CK(cudaGetLastError());
+    }
+    DetectArgs da;
+    da.frames = (const DetectFrameDev *)(A + o_desc);
+    da.tile_offset = (const int32_t *)(A + o_to);
+    da.n_frames = n;
+    da.total_tiles = (int32_t)tiles;
+    da.rS = rS; da.rR = rR; da.dR = dR; da.annulus = P.annulus; da.cap = dR + P.annulus + 1;
+    da.th2 = P.t_high * P.t_high;
+    da.tl2 = P.t_low * P.t_low;
+    da.length = P.length;
+    da.Lambda = P.Lambda;
+    std::memset(da.wS, 0, sizeof(da.wS));
+    std::memset(da.wR, 0, sizeof(da.wR));
+    gauss_taps(P.sigma, da.wS);
+    gauss_taps(P.rho, da.wR);
+    const size_t sm_dist = detect_dist_smem(da.cap), sm_tensor = detect_tensor_smem(rS, rR);
+    CK(cudaFuncSetAttribute(detect_dist_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_dist));
+    CK(cudaFuncSetAttribute(detect_tensor_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_tensor));
+    const unsigned g = (unsigned)tiles;
+    detect_dist_kernel<<<g, DET_THREADS, sm_dist, st>>>(da);
+    CK(cudaGetLastError());
+    detect_tensor_kernel<<<g, DET_THREADS, sm_tensor, st>>>(da);
+    CK(cudaGetLastError());
+    detect_union_kernel<<<g, DET_THREADS, 0, st>>>(da);
+    CK(cudaGetLastError());
+    detect_mark_kernel<<<g, DET_THREADS, 0, st>>>(da);
+    CK(cudaGetLastError());
+    detect_accept_kernel<<<g, DET_THREADS, 0, st>>>(da);
+    CK(cudaGetLastError());
+    detect_scan_kernel<<<(unsigned)n, DET_SCAN_THREADS, 0, st>>>(da);
+    CK(cudaGetLastError());
+    detect_write_kernel<<<g, DET_THREADS, 0, st>>>(da);
+    CK(cudaGetLastError());
+    return GF_OK;
+}
+
+gf_status gf_detect_splines(gf_ctx *ctx, const gf_detect_frame *frame, const gf_detect_params *params, void *stream)
+{
+    return gf_detect_splines_batched(ctx, 1, frame, params, stream);
 }
 
 gf_status gf_guide_from_angle(gf_ctx *ctx, int H, int W, const uint8_t *labels, const float *mag, const float *phi,

@@ -1,7 +1,9 @@
 // Guide field from splines (Guidefill, arxiv 1611.05319, Section 3.3) for sm_103a.
 //
-// g(x) = t_Gamma * exp(-d(x, Gamma)^2 / (2 eta^2)) for the nearest polyline
-// segment Gamma when d <= 3 eta, else 0, at every hole pixel.
+// g(x) = w_Gamma t_Gamma * exp(-d(x, Gamma)^2 / (2 eta^2)) for the nearest
+// polyline segment Gamma when d <= 3 eta, else 0, at every hole pixel; w_Gamma =
+// |g_Gamma| is the spline's weight (1 unless given, e.g. the coherence factor of
+// detected splines).
 //
 // Two kernels per request:
 //   bin_kernel    one thread per polyline point: the segment starting there is
@@ -17,7 +19,7 @@
 // depend on the machine; the returned value is evaluated in FP64 for the
 // chosen segment and rounded once to FP32.
 
-#include "gf_internal.cuh"
+#include "gf_detect.cuh"
 
 namespace gf {
 
@@ -77,6 +79,7 @@ __global__ void __launch_bounds__(256) bin_kernel(const __grid_constant__ GuideA
         s[4] = __ddiv_rn(1.0, __dmul_rn(len, len));
         s[5] = __ddiv_rn(dvx, len);
         s[6] = __ddiv_rn(dvy, len);
+        s[7] = 1.0;  // the spline's weight, set by spline_weight_kernel when given
     }
     float grow = 3.0f * a.eta + 1.0f;
     float xmin = fminf(A.x, B.x) - grow, xmax = fmaxf(A.x, B.x) + grow;
@@ -263,7 +266,7 @@ __global__ void __launch_bounds__(256) guide_kernel(const __grid_constant__ Guid
             // with the reciprocals 1/|v|^2 and 1/(2 eta^2) precomputed in FP64
             const double *s = F.seg64 + 8 * (size_t)bs;
             const double ax = __ldcg(&s[0]), ay = __ldcg(&s[1]), vx = __ldcg(&s[2]), vy = __ldcg(&s[3]);
-            const double inv_l2 = __ldcg(&s[4]), tx = __ldcg(&s[5]), ty = __ldcg(&s[6]);
+            const double inv_l2 = __ldcg(&s[4]), tx = __ldcg(&s[5]), ty = __ldcg(&s[6]), sw = __ldcg(&s[7]);
             const double wx = __dsub_rn((double)x, ax), wy = __dsub_rn((double)y, ay);
             double t = __dmul_rn(__dadd_rn(__dmul_rn(wx, vx), __dmul_rn(wy, vy)), inv_l2);
             if (t < 0.0) t = 0.0;
@@ -271,10 +274,29 @@ __global__ void __launch_bounds__(256) guide_kernel(const __grid_constant__ Guid
             const double qx = __dsub_rn(wx, __dmul_rn(t, vx)), qy = __dsub_rn(wy, __dmul_rn(t, vy));
             const double d2 = __dadd_rn(__dmul_rn(qx, qx), __dmul_rn(qy, qy));
             const double ev = exp(-__dmul_rn(d2, a.k2));
-            out.x = (float)__dmul_rn(tx, ev);
-            out.y = (float)__dmul_rn(ty, ev);
+            out.x = (float)__dmul_rn(__dmul_rn(tx, ev), sw);
+            out.y = (float)__dmul_rn(__dmul_rn(ty, ev), sw);
         }
         F.guide[(size_t)y * F.W + x] = out;
+    }
+}
+
+// The weight of the spline holding each segment, for the frames of one chunk
+// that have weights: one CTA per frame, after bin_kernel.
+__global__ void __launch_bounds__(256) spline_weight_kernel(const __grid_constant__ GuideArgs a,
+                                                            const __grid_constant__ WeightChunk c)
+{
+    const float *w = c.w[blockIdx.x];
+    if (!w) return;
+    const SplineFrameDev &F = a.frames[c.first + blockIdx.x];
+    for (int i = threadIdx.x; i + 1 < F.n_points; i += blockDim.x) {
+        int lo = 0, hi = F.n_splines;
+        while (hi - lo > 1) {
+            const int mid = (lo + hi) >> 1;
+            if (__ldg(&F.offsets[mid]) <= i) lo = mid; else hi = mid;
+        }
+        if (F.n_splines <= 0 || i < __ldg(&F.offsets[0]) || i + 1 >= __ldg(&F.offsets[lo + 1])) continue;
+        F.seg64[8 * (size_t)i + 7] = (double)__ldg(&w[lo]);
     }
 }
 

@@ -53,6 +53,8 @@ def test_status_strings_and_argument_errors_without_gpu(built_lib):
     assert lib.gf_fill_batched(None, 1, None, None, None, None) == -1
     lib.gf_guidance_batched.restype = C.c_int
     assert lib.gf_guidance_batched(None, 1, None, C.c_float(3.0), None) == -1
+    lib.gf_detect_splines_batched.restype = C.c_int
+    assert lib.gf_detect_splines_batched(None, 1, None, None, None) == -1
 
 
 def test_struct_layouts_match_header(tmp_path):
@@ -62,10 +64,13 @@ def test_struct_layouts_match_header(tmp_path):
     if not shutil.which("gcc"):
         pytest.skip("gcc not available")
     src = tmp_path / "sz.c"
-    src.write_text('#include <stdio.h>\n#include "%s"\nint main(void){printf("%%zu %%zu %%zu %%zu",'
-                   'sizeof(gf_frame),sizeof(gf_params),sizeof(gf_spline_frame),sizeof(gf_stats));return 0;}' % HEADER)
+    src.write_text('#include <stdio.h>\n#include <stddef.h>\n#include "%s"\nint main(void){printf("%%zu %%zu %%zu %%zu",'
+                   'sizeof(gf_frame),sizeof(gf_params),sizeof(gf_spline_frame),sizeof(gf_stats));'
+                   'printf(" %%zu %%zu %%zu",sizeof(gf_detect_params),sizeof(gf_detect_frame),'
+                   'offsetof(gf_detect_frame,result));return 0;}' % HEADER)
     exe = tmp_path / "sz"
     subprocess.run(["gcc", str(src), "-o", str(exe)], check=True)
     sizes = [int(v) for v in subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split()]
     from paper_1611_05319_gb300 import _lib
-    assert sizes == [C.sizeof(_lib.Frame), C.sizeof(_lib.Params), C.sizeof(_lib.SplineFrame), _lib.STATS_BYTES]
+    assert sizes == [C.sizeof(_lib.Frame), C.sizeof(_lib.Params), C.sizeof(_lib.SplineFrame), _lib.STATS_BYTES,
+                     C.sizeof(_lib.DetectParams), C.sizeof(_lib.DetectFrame), _lib.DetectFrame.result.offset]
