@@ -109,6 +109,30 @@ def oracle_sample(n_frames, cores):
     return px / wall, wall, px
 
 
+def _oracle_detect_frame(seed):
+    import oracle
+    from synth import configs
+    f = configs.batch_frame(seed)
+    t0 = time.perf_counter()
+    r = oracle.detect_splines(f["rgb"], f["labels"])
+    return time.perf_counter() - t0, r["count"]
+
+
+def oracle_detect_sample(cores):
+    """Times the oracle's spline detection (Section 3.3) on frames of the batch,
+    one frame per process.  Returns the cpu_baseline record of that leg."""
+    seeds = [SEED0 + i for i in range(cores)]
+    ctx = mp.get_context("spawn")
+    with ctx.Pool(cores) as pool:
+        t0 = time.perf_counter()
+        res = pool.map(_oracle_detect_frame, seeds)
+        wall = time.perf_counter() - t0
+    per = statistics.mean(r[0] for r in res)
+    return {"value": 1920 * 1080 / per / 1e6, "unit": "frame Mpx/s per core", "cores": cores, "kind": "oracle",
+            "sample": f"frames {seeds[0]}-{seeds[-1]} of the batch, one per process; mean {per:.2f} s per frame, "
+                      f"{wall:.2f} s wall"}
+
+
 def host_cores():
     try:
         return len(os.sched_getaffinity(0))
@@ -192,6 +216,9 @@ def main():
         cpu = {"value": v, "unit": "filled px/s", "cores": cores, "kind": "oracle",
                "sample": f"first {args.cpu_sample} frames of the batch (guide field + fill, FP64), one frame per "
                          f"process on {cores} host cores; {px} px in {wall:.2f} s"}
+    cpu_detect = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline and not args.no_extra:
+        cpu_detect = oracle_detect_sample(min(host_cores(), 4))
 
     import numpy as np
 
@@ -353,7 +380,7 @@ def main():
         e2e = {"value": world * fe / w, "unit": "filled px/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                "ms_per_step": w * 1e3, "call": "gf_fill_batched_host (pinned host buffers, splines in)"}
 
-    extra4k = adjoint = single = complexity = theorem1 = data_term = None
+    extra4k = adjoint = single = complexity = theorem1 = data_term = detect = None
     if rank == 0 and not args.no_extra:
         single = leg_1080(ctx, dev, stream, max(10, args.extra_steps))
         extra4k = leg_4k(ctx, dev, stream, args.extra_steps)
@@ -361,6 +388,7 @@ def main():
         complexity = leg_complexity(ctx, dev, stream, args.extra_steps)
         theorem1 = leg_theorem1(dev)
         data_term = leg_data_term(ctx, dev, stream, max(3, args.extra_steps))
+        detect = leg_detect(ctx, dev, stream, max(3, args.extra_steps), rgba, labels, cpu_detect)
 
     if rank != 0:
         if dist:
@@ -380,6 +408,7 @@ def main():
         "gpu_launches": launches_per_step * K, "clocks": clocks,
         "single_1080": single, "tracked_vs_rescan_4k": extra4k, "adjoint_16x512": adjoint,
         "complexity_line": complexity, "theorem1_curves": theorem1, "data_term_1080": data_term,
+        "spline_detection_batch": detect,
         "status_errors": bad,
     }
     print(json.dumps(line), flush=True)
@@ -676,6 +705,86 @@ def leg_data_term(ctx, dev, stream, steps):
                      "filled": int(st["filled"])}
     out["workload"] = "1920x1080 frame of the single-frame case (seed 2), eps=3, mu=50, guide field from its splines"
     return out
+
+
+def _detect_alg_bytes(lab, dR, annulus, halo):
+    """Algorithmic bytes of the detection on one frame: every label (1 B, to find
+    the hole) and the RGBA (16 B) of each pixel within the tensor window of an
+    annulus pixel (Chebyshev radius halo = ceil(2 sigma) + ceil(2 rho) + 1 + 1
+    for the suppression neighbours); outputs are negligible."""
+    import numpy as np
+    from scipy import ndimage
+    dh = ndimage.distance_transform_cdt((lab != 1).astype(np.int32), metric="chessboard")
+    ann = (lab == 0) & (np.abs(dh - dR) <= annulus)
+    win = ndimage.maximum_filter(ann.astype(np.uint8), size=2 * halo + 1, mode="constant") > 0
+    return int(lab.size) + 16 * int(win.sum()), int(ann.sum())
+
+
+def leg_detect(ctx, dev, stream, steps, rgba, labels, cpu):
+    """Automatic spline detection (Section 3.3) on the 64 frames of the batched
+    workload in one batched call (sigma = 2, rho = 4, ring 14 px, annulus 2,
+    Canny thresholds 0.04 / 0.015), and detection followed by the guide field
+    from the detected splines (coherence-weighted), both timed with events."""
+    import ctypes as C
+
+    import numpy as np
+    import torch
+
+    from paper_1611_05319_gb300 import _lib
+    n, H, W = labels.shape
+    m = 4096
+    pts = torch.zeros((n, m, 2, 2), dtype=torch.float32, device=dev)
+    wt = torch.zeros((n, m), dtype=torch.float32, device=dev)
+    off = torch.zeros((n, m + 1), dtype=torch.int32, device=dev)
+    res = torch.zeros((n, 2), dtype=torch.int32, device=dev)
+    guide = torch.zeros((n, H, W, 2), dtype=torch.float32, device=dev)
+    fr = (_lib.DetectFrame * n)()
+    sf = (_lib.SplineFrame * n)()
+    for i in range(n):
+        fr[i] = _lib.DetectFrame(H, W, rgba[i].data_ptr(), labels[i].data_ptr(), m, pts[i].data_ptr(),
+                                 wt[i].data_ptr(), off[i].data_ptr(), None, None, res[i].data_ptr())
+        sf[i] = _lib.SplineFrame(H, W, labels[i].data_ptr(), m, 2 * m, off[i].data_ptr(), pts[i].data_ptr(),
+                                 guide[i].data_ptr(), wt[i].data_ptr())
+    prm = _lib.make_detect_params()
+    L = _lib.lib()
+    sp = C.c_void_p(stream.cuda_stream)
+
+    def detect():
+        _lib.check(L.gf_detect_splines_batched(ctx._h, n, fr, C.byref(prm), sp), "detect", ctx._h)
+
+    def detect_and_guide():
+        detect()
+        _lib.check(L.gf_guidance_batched(ctx._h, n, sf, C.c_float(3.0), sp), "guidance", ctx._h)
+
+    for _ in range(3):
+        detect_and_guide()
+    ms = _time(detect, steps, stream)
+    ms_g = _time(detect_and_guide, steps, stream)
+    r = res.cpu().numpy()
+    if (r[:, 1] != 0).any():
+        raise RuntimeError("spline detection reported a device status")
+    lab_h = labels.cpu().numpy()
+    alg, ann = 0, 0
+    for i in range(n):
+        a, b = _detect_alg_bytes(lab_h[i], 14, 2, 4 + 8 + 1 + 1)
+        alg += a
+        ann += b
+    try:
+        peak = float(json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["hbm_gbs"])
+        src = "measured"
+    except Exception:
+        peak, src = 6800.0, "fallback"
+    ach = alg / (ms / 1e3) / 1e9
+    chunks = (n + 63) // 64
+    return {"ms_per_batch": ms, "frames_per_s": n / (ms / 1e3), "frame_px_per_s": n * H * W / (ms / 1e3),
+            "splines": int(r[:, 0].sum()), "annulus_px": ann,
+            "detect_plus_guide_field_ms": ms_g,
+            "stage_roofline": {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
+                               "alg_bytes_per_call": alg, "peak_source": src,
+                               "note": "whole detection call (7 kernels + descriptor upload) timed with events"},
+            "gpu_launches_per_call": chunks + 7, "cpu_baseline": cpu,
+            "workload": f"{n} frames {W}x{H} of the batched workload, one gf_detect_splines_batched call; "
+                        "sigma=2, rho=4, ring 14 px, annulus 2, t_high 0.04, t_low 0.015, length 48 px"}
 
 
 def leg_adjoint(ctx, dev, stream, steps):

@@ -15,9 +15,10 @@
  *      tanh((lambda+ - lambda-) / Lambda) of g_Gamma.
  * Plain loops over the whole image, one step at a time.  Every decision that
  * turns real numbers into a set (a threshold, a suppression, a sign, the ring)
- * uses FP32 values formed with + - * / sqrt and comparisons only, no
- * contraction, so a second implementation doing the same operations in the same
- * order reaches the same sets.
+ * uses FP32 values formed with correctly rounded operations only (+ - * / sqrt,
+ * fused multiply-add where stated) and comparisons, no other contraction, so a
+ * second implementation doing the same operations in the same order reaches
+ * the same sets.
  *
  * Readings where the section is not specific:
  *  - distances are Chebyshev distances: d_hole to the nearest hole pixel
@@ -30,10 +31,12 @@
  *  - annulus: known pixels with |d_hole - dR| <= annulus (bystander pixels are
  *    "not the current object" and ignored);
  *  - the image is RGB: u_sigma per channel, gradient outer products summed over
- *    the channels (the multichannel structure tensor);
+ *    the channels in order R, G, B by fused multiply-add (the multichannel
+ *    structure tensor);
  *  - g_s: truncated to radius r = ceil(2 s) (the (4 s + 1) window), taps
  *    exp(-i^2 / (2 s^2)) in FP64 rounded to FP32 and divided by their FP32 sum;
  *    applied separably, along rows then along columns, taps in order -r..r,
+ *    each accumulated by a fused multiply-add (one rounding per tap),
  *    coordinates clamped to the image;
  *  - gradient: central differences (u(x+1) - u(x-1)) / 2, one-sided at the
  *    image border;
@@ -101,14 +104,14 @@ static void blur3(int H, int W, const float *in, float *out, float s, float *tmp
         for (int x = 0; x < W; x++)
             for (int c = 0; c < 3; c++) {
                 float a = 0.0f;
-                for (int i = -r; i <= r; i++) a = a + w[i + r] * in[((size_t)y * W + iclamp(x + i, 0, W - 1)) * 3 + c];
+                for (int i = -r; i <= r; i++) a = fmaf(w[i + r], in[((size_t)y * W + iclamp(x + i, 0, W - 1)) * 3 + c], a);
                 tmp[((size_t)y * W + x) * 3 + c] = a;
             }
     for (int y = 0; y < H; y++)
         for (int x = 0; x < W; x++)
             for (int c = 0; c < 3; c++) {
                 float a = 0.0f;
-                for (int i = -r; i <= r; i++) a = a + w[i + r] * tmp[((size_t)iclamp(y + i, 0, H - 1) * W + x) * 3 + c];
+                for (int i = -r; i <= r; i++) a = fmaf(w[i + r], tmp[((size_t)iclamp(y + i, 0, H - 1) * W + x) * 3 + c], a);
                 out[((size_t)y * W + x) * 3 + c] = a;
             }
 }
@@ -194,9 +197,9 @@ int oracle_detect_splines(int H, int W, const float *rgb, const uint8_t *lab, co
             for (int c = 0; c < 3; c++) {
                 float gx = sx > 0.0f ? (us[((size_t)y * W + xr) * 3 + c] - us[((size_t)y * W + xl) * 3 + c]) / sx : 0.0f;
                 float gy = sy > 0.0f ? (us[((size_t)yd * W + x) * 3 + c] - us[((size_t)yu * W + x) * 3 + c]) / sy : 0.0f;
-                jxx = jxx + gx * gx;
-                jxy = jxy + gx * gy;
-                jyy = jyy + gy * gy;
+                jxx = fmaf(gx, gx, jxx);
+                jxy = fmaf(gx, gy, jxy);
+                jyy = fmaf(gy, gy, jyy);
             }
             size_t p = (size_t)y * W + x;
             T[p * 3 + 0] = jxx;

@@ -959,14 +959,17 @@ gf_status gf_detect_splines_batched(gf_ctx *ctx, int n, const gf_detect_frame *f
     // scratch per frame: distances, tile flags, edge classes, union-find, candidates, row-segment masks
     std::vector<DetectFrameDev> hd(n);
     std::vector<int32_t> hto(n + 1);
-    std::vector<size_t> o_dist(n), o_act(n), o_edge(n), o_par(n), o_mark(n), o_cand(n), o_accm(n), o_accp(n);
+    std::vector<size_t> o_mask(n), o_dist(n), o_edge(n), o_par(n), o_mark(n), o_cand(n), o_accm(n), o_accp(n);
+    std::vector<int32_t> hwo(n + 1);
+    int64_t words = 0;
     size_t pos = 0;
     int64_t tiles = 0;
     for (int i = 0; i < n; i++) {
         const size_t np = (size_t)frames[i].H * frames[i].W;
         const int NBX = (frames[i].W + DT - 1) / DT, NBY = (frames[i].H + DT - 1) / DT;
+        const int NWF = (frames[i].W + 31) / 32;
+        o_mask[i] = pos; pos = align_up(pos + 8 * (size_t)frames[i].H * NWF, 256);
         o_dist[i] = pos; pos = align_up(pos + 2 * np, 256);
-        o_act[i] = pos; pos = align_up(pos + (size_t)NBX * NBY, 256);
         o_edge[i] = pos; pos = align_up(pos + np, 256);
         o_par[i] = pos; pos = align_up(pos + 4 * np, 256);
         o_mark[i] = pos; pos = align_up(pos + 4 * np, 256);
@@ -975,11 +978,20 @@ gf_status gf_detect_splines_batched(gf_ctx *ctx, int n, const gf_detect_frame *f
         o_accp[i] = pos; pos = align_up(pos + 4 * (size_t)frames[i].H * NBX, 256);
         hto[i] = (int32_t)tiles;
         tiles += (int64_t)NBX * NBY;
+        hwo[i] = (int32_t)words;
+        words += (int64_t)frames[i].H * NWF;
     }
     hto[n] = (int32_t)tiles;
-    if (tiles >= INT32_MAX) return GF_ERR_ARG;
+    hwo[n] = (int32_t)words;
+    if (tiles >= INT32_MAX || words >= INT32_MAX) return GF_ERR_ARG;
     const size_t o_desc = pos; pos = align_up(pos + sizeof(DetectFrameDev) * (size_t)n, 256);
     const size_t o_to = pos; pos = align_up(pos + 4 * (size_t)(n + 1), 256);
+    const size_t o_wo = pos; pos = align_up(pos + 4 * (size_t)(n + 1), 256);
+    const size_t o_list = pos; pos = align_up(pos + 4 * (size_t)tiles, 256);
+    const size_t o_slist = pos; pos = align_up(pos + 4 * (size_t)tiles, 256);
+    const size_t o_cnt = pos; pos = align_up(pos + 8, 256);                 // active, slow counts
+    const size_t o_flags = pos; pos = align_up(pos + 2 * (size_t)tiles, 256);  // hole_t, act_t (cleared)
+    const size_t o_slow = pos; pos = align_up(pos + (size_t)tiles, 256);       // slow_t
     gf_status s = ensure(ctx, ctx->darena, pos);
     if (s != GF_OK) return s;
     char *A = (char *)ctx->darena.ptr;
@@ -989,8 +1001,12 @@ gf_status gf_detect_splines_batched(gf_ctx *ctx, int n, const gf_detect_frame *f
         d.H = f.H; d.W = f.W;
         d.NBX = (f.W + DT - 1) / DT; d.NBY = (f.H + DT - 1) / DT;
         d.rgba = (const float4 *)f.rgba; d.labels = f.labels;
+        d.masks = (uint2 *)(A + o_mask[i]);
+        d.hole_t = (uint8_t *)(A + o_flags) + hto[i];
+        d.act_t = (uint8_t *)(A + o_flags) + tiles + hto[i];
+        d.slow_t = (uint8_t *)(A + o_slow) + hto[i];
+        d.NWF = (f.W + 31) / 32;
         d.dist = (uchar2 *)(A + o_dist[i]);
-        d.active = (uint8_t *)(A + o_act[i]);
         d.edge = (uint8_t *)(A + o_edge[i]);
         d.parent = (int32_t *)(A + o_par[i]);
         d.mark = (int32_t *)(A + o_mark[i]);
@@ -999,27 +1015,35 @@ gf_status gf_detect_splines_batched(gf_ctx *ctx, int n, const gf_detect_frame *f
         d.accpos = (uint32_t *)(A + o_accp[i]);
         d.pts = (float2 *)f.pts; d.weight = f.weight; d.offsets = f.offsets; d.base = f.base;
         d.edges_out = f.edges; d.result = f.result;
-        d.max_splines = f.max_splines; d.pad = 0;
+        d.max_splines = f.max_splines;
         hd[i] = d;
     }
     for (int c0 = 0; c0 < n; c0 += DET_CHUNK) {
         static thread_local DetectChunk ch;
         ch.dst_frames = (DetectFrameDev *)(A + o_desc);
         ch.dst_to = (int32_t *)(A + o_to);
+        ch.dst_wo = (int32_t *)(A + o_wo);
         ch.first = c0;
         ch.count = std::min(DET_CHUNK, n - c0);
         ch.last_chunk = (c0 + ch.count == n) ? 1 : 0;
         for (int i = 0; i < ch.count; i++) {
             ch.frames[i] = hd[c0 + i];
             ch.to[i] = hto[c0 + i];
+            ch.wo[i] = hwo[c0 + i];
         }
         ch.to[ch.count] = hto[c0 + ch.count];
+        ch.wo[ch.count] = hwo[c0 + ch.count];
         upload_detect_kernel<<<1, 64, 0, st>>>(ch);
         CK(cudaGetLastError());
     }
     DetectArgs da;
     da.frames = (const DetectFrameDev *)(A + o_desc);
     da.tile_offset = (const int32_t *)(A + o_to);
+    da.active_list = (int32_t *)(A + o_list);
+    da.active_count = (int32_t *)(A + o_cnt);
+    da.slow_list = (int32_t *)(A + o_slist);
+    da.slow_count = (int32_t *)(A + o_cnt) + 1;
+    da.word_offset = (const int32_t *)(A + o_wo);
     da.n_frames = n;
     da.total_tiles = (int32_t)tiles;
     da.rS = rS; da.rR = rR; da.dR = dR; da.annulus = P.annulus; da.cap = dR + P.annulus + 1;
@@ -1032,22 +1056,38 @@ gf_status gf_detect_splines_batched(gf_ctx *ctx, int n, const gf_detect_frame *f
     gauss_taps(P.sigma, da.wS);
     gauss_taps(P.rho, da.wR);
     const size_t sm_dist = detect_dist_smem(da.cap), sm_tensor = detect_tensor_smem(rS, rR);
+    const void *tensor = detect_tensor_entry(rS);
+    if (!tensor) return GF_ERR_ARG;
     CK(cudaFuncSetAttribute(detect_dist_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_dist));
-    CK(cudaFuncSetAttribute(detect_tensor_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_tensor));
-    const unsigned g = (unsigned)tiles;
-    detect_dist_kernel<<<g, DET_THREADS, sm_dist, st>>>(da);
+    CK(cudaFuncSetAttribute(tensor, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_tensor));
+    // persistent grids over the active tiles: as many CTAs as fit on the SMs at once
+    int per_sm = 0;
+    CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, tensor, DET_THREADS, sm_tensor));
+    const unsigned g_tensor = (unsigned)std::min<int64_t>(tiles, (int64_t)std::max(per_sm, 1) * ctx->sm_count);
+    const unsigned g_list = (unsigned)std::min<int64_t>(tiles, 8 * (int64_t)ctx->sm_count);
+    int per_sm_dist = 0;
+    CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_dist, detect_dist_kernel, DET_THREADS, sm_dist));
+    const unsigned g_dist = (unsigned)std::min<int64_t>(tiles, (int64_t)std::max(per_sm_dist, 1) * ctx->sm_count);
+    CK(cudaMemsetAsync(A + o_cnt, 0, 8, st));
+    CK(cudaMemsetAsync(A + o_flags, 0, 2 * (size_t)tiles, st));
+    for (int i = 0; i < n; i++)
+        if (frames[i].edges) CK(cudaMemsetAsync(frames[i].edges, 0, (size_t)frames[i].H * frames[i].W, st));
+    detect_pack_kernel<<<(unsigned)((words + 255) / 256), 256, 0, st>>>(da, (int)words);
     CK(cudaGetLastError());
-    detect_tensor_kernel<<<g, DET_THREADS, sm_tensor, st>>>(da);
+    detect_classify_kernel<<<(unsigned)((tiles + 255) / 256), 256, 0, st>>>(da);
     CK(cudaGetLastError());
-    detect_union_kernel<<<g, DET_THREADS, 0, st>>>(da);
+    detect_dist_kernel<<<g_dist, DET_THREADS, sm_dist, st>>>(da);
     CK(cudaGetLastError());
-    detect_mark_kernel<<<g, DET_THREADS, 0, st>>>(da);
+    CK(launch_detect_tensor(rS, g_tensor, sm_tensor, st, da));
+    detect_union_kernel<<<g_list, DET_THREADS, 0, st>>>(da);
     CK(cudaGetLastError());
-    detect_accept_kernel<<<g, DET_THREADS, 0, st>>>(da);
+    detect_mark_kernel<<<g_list, DET_THREADS, 0, st>>>(da);
+    CK(cudaGetLastError());
+    detect_accept_kernel<<<g_list, DET_THREADS, 0, st>>>(da);
     CK(cudaGetLastError());
     detect_scan_kernel<<<(unsigned)n, DET_SCAN_THREADS, 0, st>>>(da);
     CK(cudaGetLastError());
-    detect_write_kernel<<<g, DET_THREADS, 0, st>>>(da);
+    detect_write_kernel<<<g_list, DET_THREADS, 0, st>>>(da);
     CK(cudaGetLastError());
     return GF_OK;
 }
