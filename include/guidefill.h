@@ -233,14 +233,15 @@ gf_status gf_guidance_batched(gf_ctx *ctx, int n, const gf_spline_frame *frames,
  * edge a straight spline of length `length` from the pixel along the minor
  * eigenvector v- of the structure tensor J_{sigma,rho} (eq. structureTensor) at
  * that pixel, signed to point into D_h, with the weight tanh((lambda+ -
- * lambda-)/Lambda) of g_Gamma.  Definitions, all in FP32 with no contraction
- * unless stated:
+ * lambda-)/Lambda) of g_Gamma.  Definitions, all in FP32 with correctly
+ * rounded operations and no contraction beyond the fused multiply-adds stated:
  *  - u_sigma = g_sigma * u per colour channel (R, G, B; alpha unused); g_s has
  *    radius ceil(2 s) (window 4 s + 1), taps exp(-i^2/(2 s^2)) (FP64, rounded)
  *    divided by their FP32 sum, applied along rows then columns, taps in order
- *    -r..r, image coordinates clamped;
+ *    -r..r, each accumulated by a fused multiply-add, image coordinates clamped;
  *  - gradient by central differences (one-sided at the border); T = sum over
- *    channels of grad u_sigma (x) grad u_sigma; J = g_rho * T (same blur);
+ *    channels R, G, B of grad u_sigma (x) grad u_sigma, each product accumulated
+ *    by a fused multiply-add; J = g_rho * T (same blur);
  *  - Canny: m2 = Txx + Tyy; direction from d = Txx - Tyy, e = 2 Txy quantised
  *    to 0/45/90/135 degrees (|e| <= d: 0; |e| <= -d: 90; e > 0: 45; else 135);
  *    kept by suppression when m2 >= m2 of both neighbours along it; strong when
