@@ -44,9 +44,12 @@ struct gf_ctx {
     int last_split_m = 0, last_split_cs = 0, last_split_nc = 0;
     cudaStream_t aux = nullptr;                   // the second launch's stream
     cudaEvent_t fork_ev = nullptr, join_ev = nullptr;
-    // host-buffer path: copy streams and the events of its chunk pipeline
+    // host-buffer path: copy streams, the events of its chunk pipeline, and per
+    // chunk a stream and scratch for its guide field and fill (chunks overlap)
     cudaStream_t copy_in = nullptr, copy_out = nullptr;
     std::vector<cudaEvent_t> pipe_ev;
+    std::vector<cudaStream_t> pipe_st;
+    std::vector<DevBuf> pipe_fill, pipe_guide;
     // autotuned launch shapes keyed by (n frames, H, W, eps, flags)
     struct Tuned {
         uint64_t key;
@@ -286,6 +289,7 @@ void gf_destroy(gf_ctx *ctx)
     if (ctx->copy_in) cudaStreamDestroy(ctx->copy_in);
     if (ctx->copy_out) cudaStreamDestroy(ctx->copy_out);
     for (cudaEvent_t ev : ctx->pipe_ev) cudaEventDestroy(ev);
+    for (cudaStream_t s : ctx->pipe_st) cudaStreamDestroy(s);
     if (ctx->fork_ev) cudaEventDestroy(ctx->fork_ev);
     if (ctx->join_ev) cudaEventDestroy(ctx->join_ev);
     cudaDeviceSynchronize();
@@ -295,6 +299,10 @@ void gf_destroy(gf_ctx *ctx)
     if (ctx->io.ptr) cudaFree(ctx->io.ptr);
     if (ctx->aarena.ptr) cudaFree(ctx->aarena.ptr);
     if (ctx->darena.ptr) cudaFree(ctx->darena.ptr);
+    for (DevBuf &b : ctx->pipe_fill)
+        if (b.ptr) cudaFree(b.ptr);
+    for (DevBuf &b : ctx->pipe_guide)
+        if (b.ptr) cudaFree(b.ptr);
     delete ctx;
 }
 
@@ -371,8 +379,9 @@ int gf_max_active_clusters(gf_ctx *ctx, float eps, int cluster_size)
 
 static gf_status enqueue_fill(gf_ctx *ctx, int n, const gf_frame *frames, const gf_params *prm,
                               gf_stats *dev_stats, cudaStream_t stream, cudaEvent_t ev0 = nullptr,
-                              cudaEvent_t ev1 = nullptr, bool allow_graph = true)
+                              cudaEvent_t ev1 = nullptr, bool allow_graph = true, DevBuf *scratch = nullptr)
 {
+    DevBuf &arena = scratch ? *scratch : ctx->arena;
     // ---- layout of the scratch arena
     std::vector<size_t> off_U(n), off_Q(n), off_F(n), off_S(n), off_L(n);
     std::vector<int> ntiles(n);
@@ -443,9 +452,9 @@ static gf_status enqueue_fill(gf_ctx *ctx, int n, const gf_frame *frames, const 
 
     const size_t off_ctl = pos; pos = align_up(pos + sizeof(GroupCtl) * (size_t)ncall, 256);
     const size_t off_lists = pos; pos = align_up(pos + 4 * (size_t)3 * list_cap * ncall, 256);
-    gf_status st = ensure(ctx, ctx->arena, pos);
+    gf_status st = ensure(ctx, arena, pos);
     if (st != GF_OK) return st;
-    char *A = (char *)ctx->arena.ptr;
+    char *A = (char *)arena.ptr;
 
     // ---- frame descriptors (uploaded by value through kernel parameters)
     std::vector<FrameDev> hdv(n);
@@ -524,7 +533,7 @@ static gf_status enqueue_fill(gf_ctx *ctx, int n, const gf_frame *frames, const 
     key = fnv(key, &snc, sizeof(snc));
     key = fnv(key, &n, sizeof(n));
     for (int i = 0; i < n; i++) key = fnv(key, &frames[i].rgba, sizeof(void *));
-    key = fnv(key, &ctx->arena.ptr, sizeof(void *));
+    key = fnv(key, &arena.ptr, sizeof(void *));
 
     const bool graph = allow_graph && ctx->use_graph && stream != nullptr;
     if (graph && ctx->gexec && ctx->gexec_fill && ctx->gkey == key) {
@@ -797,7 +806,17 @@ gf_status gf_fill(gf_ctx *ctx, const gf_frame *frame, const gf_params *params, g
     return gf_fill_batched(ctx, 1, frame, params, dev_stats, stream);
 }
 
+static gf_status guidance_impl(gf_ctx *ctx, DevBuf &garena, int n, const gf_spline_frame *frames, float eta,
+                               void *stream);
+
 gf_status gf_guidance_batched(gf_ctx *ctx, int n, const gf_spline_frame *frames, float eta, void *stream)
+{
+    if (!ctx) return GF_ERR_ARG;
+    return guidance_impl(ctx, ctx->garena, n, frames, eta, stream);
+}
+
+static gf_status guidance_impl(gf_ctx *ctx, DevBuf &garena, int n, const gf_spline_frame *frames, float eta,
+                               void *stream)
 {
     if (!ctx || n <= 0 || !frames || !(eta > 0.0f) || !std::isfinite(eta)) return GF_ERR_ARG;
     for (int i = 0; i < n; i++) {
@@ -825,9 +844,9 @@ gf_status gf_guidance_batched(gf_ctx *ctx, int n, const gf_spline_frame *frames,
     const size_t off_desc = pos; pos = align_up(pos + sizeof(SplineFrameDev) * (size_t)n, 256);
     const size_t off_po = pos; pos = align_up(pos + 4 * (size_t)(n + 1), 256);
     const size_t off_bo = pos; pos = align_up(pos + 4 * (size_t)(n + 1), 256);
-    gf_status s = ensure(ctx, ctx->garena, pos);
+    gf_status s = ensure(ctx, garena, pos);
     if (s != GF_OK) return s;
-    char *A = (char *)ctx->garena.ptr;
+    char *A = (char *)garena.ptr;
     std::vector<SplineFrameDev> hdv(n);
     std::vector<int32_t> hpov(n + 1), hbov(n + 1);
     SplineFrameDev *hd = hdv.data();
@@ -1291,13 +1310,14 @@ gf_status gf_fill_batched_host(gf_ctx *ctx, int n, const int32_t *H, const int32
     if (s != GF_OK) return s;
     char *A = (char *)ctx->io.ptr;
     cudaStream_t st = (cudaStream_t)stream;
-    // Chunk pipeline: the frames' inputs are copied in on one stream, each chunk is
-    // filled on `stream` as soon as its inputs have landed, and its outputs are
-    // copied out on a third stream while later chunks are still being filled, so
-    // the copies in both directions overlap each other and the compute.
-    const int nchunk = std::min(n, 4);
+    // Chunk pipeline: the frames' inputs are copied in on one stream; each chunk's
+    // guide field, fill and output copies run on a stream of their own (with
+    // scratch of their own) as soon as its inputs have landed, so chunks whose
+    // frames have long shell chains overlap the next chunks instead of delaying
+    // them.  `copy_out` only joins the chunks' streams before `stream` continues.
+    const int nchunk = std::min(n, 8);
     // frames are dealt to the chunks round-robin (position q of the pipeline order
-    // holds frame perm[q]), so that frames with long shell chains spread over them
+    // holds frame perm[q])
     std::vector<int> perm;
     perm.reserve(n);
     for (int c = 0; c < nchunk; c++)
@@ -1307,6 +1327,13 @@ gf_status gf_fill_batched_host(gf_ctx *ctx, int n, const int32_t *H, const int32
         CK(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
         ctx->pipe_ev.push_back(ev);
     }
+    while ((int)ctx->pipe_st.size() < nchunk) {
+        cudaStream_t ps;
+        CK(cudaStreamCreateWithFlags(&ps, cudaStreamNonBlocking));
+        ctx->pipe_st.push_back(ps);
+    }
+    if ((int)ctx->pipe_fill.size() < nchunk) ctx->pipe_fill.resize(nchunk);
+    if ((int)ctx->pipe_guide.size() < nchunk) ctx->pipe_guide.resize(nchunk);
     cudaEvent_t ev_start = ctx->pipe_ev[0], ev_out_done = ctx->pipe_ev[1];
     CK(cudaEventRecord(ev_start, st));  // inputs may be written by work already on `stream`
     CK(cudaStreamWaitEvent(ctx->copy_in, ev_start, 0));
@@ -1352,43 +1379,55 @@ gf_status gf_fill_batched_host(gf_ctx *ctx, int n, const int32_t *H, const int32
         CK(cudaEventRecord(ctx->pipe_ev[2 + 2 * c], ctx->copy_in));
     }
     // Unless a launch shape was set, a chunk's frames get the largest cluster size at
-    // which every one of them has its own cluster (8 CTAs for 16 frames on 152 SMs).
-    const int save_cs = ctx->cluster_size;
+    // which every one of them has its own cluster and two chunks fit on the SMs at
+    // once (4 CTAs for 8 frames on 152 SMs).  No split schedule: its second stream
+    // and events belong to the context.
+    const int save_cs = ctx->cluster_size, save_nc = ctx->n_clusters;
+    const int save_sm = ctx->split_m, save_scs = ctx->split_cs, save_snc = ctx->split_nc;
+    ctx->split_m = ctx->split_cs = ctx->split_nc = 0;
     gf_status fs = GF_OK;
     for (int c = 0; c < nchunk && fs == GF_OK; c++) {
         const int q0 = n * c / nchunk, q1 = n * (c + 1) / nchunk;
-        CK(cudaStreamWaitEvent(st, ctx->pipe_ev[2 + 2 * c], 0));
+        cudaStream_t cs_st = ctx->pipe_st[c];
+        CK(cudaStreamWaitEvent(cs_st, ctx->pipe_ev[2 + 2 * c], 0));
         std::vector<gf_spline_frame> sfc;
         for (int q = q0; q < q1; q++)
             if (from_splines[perm[q]]) sfc.push_back(sf[q]);
         if (!sfc.empty()) {
-            fs = gf_guidance_batched(ctx, (int)sfc.size(), sfc.data(), eta, stream);
+            fs = guidance_impl(ctx, ctx->pipe_guide[c], (int)sfc.size(), sfc.data(), eta, cs_st);
             if (fs != GF_OK) break;
         }
         if (save_cs == 0) {
             int cs = 16;
-            while (cs > 1 && cs * (q1 - q0) > ctx->sm_count) cs >>= 1;
+            while (cs > 1 && 2 * cs * (q1 - q0) > ctx->sm_count) cs >>= 1;
             ctx->cluster_size = cs;
+            ctx->n_clusters = 0;
         }
-        // graphs are keyed by the frame set, which changes from chunk to chunk
-        fs = enqueue_fill(ctx, q1 - q0, fr.data() + q0, params, (gf_stats *)(A + o_st) + q0, st, nullptr, nullptr,
-                          false);
+        fs = enqueue_fill(ctx, q1 - q0, fr.data() + q0, params, (gf_stats *)(A + o_st) + q0, cs_st, nullptr, nullptr,
+                          false, &ctx->pipe_fill[c]);
         ctx->cluster_size = save_cs;
+        ctx->n_clusters = save_nc;
         if (fs != GF_OK) break;
-        CK(cudaEventRecord(ctx->pipe_ev[3 + 2 * c], st));
-        CK(cudaStreamWaitEvent(ctx->copy_out, ctx->pipe_ev[3 + 2 * c], 0));
+        // the chunk's outputs leave on its own stream, so a chunk with a long shell
+        // chain holds back no other chunk's copies
         for (int q = q0; q < q1; q++) {
             const int i = perm[q];
             size_t np = (size_t)H[i] * W[i];
-            CK(cudaMemcpyAsync(host_out_rgba[i], A + o_rgba[i], 16 * np, cudaMemcpyDeviceToHost, ctx->copy_out));
-            CK(cudaMemcpyAsync(host_out_shell[i], A + o_sh[i], 4 * np, cudaMemcpyDeviceToHost, ctx->copy_out));
+            CK(cudaMemcpyAsync(host_out_rgba[i], A + o_rgba[i], 16 * np, cudaMemcpyDeviceToHost, cs_st));
+            CK(cudaMemcpyAsync(host_out_shell[i], A + o_sh[i], 4 * np, cudaMemcpyDeviceToHost, cs_st));
         }
+        CK(cudaEventRecord(ctx->pipe_ev[3 + 2 * c], cs_st));
+        CK(cudaStreamWaitEvent(ctx->copy_out, ctx->pipe_ev[3 + 2 * c], 0));
     }
+    ctx->split_m = save_sm;
+    ctx->split_cs = save_scs;
+    ctx->split_nc = save_snc;
     CK(cudaEventRecord(ev_out_done, ctx->copy_out));
     CK(cudaStreamWaitEvent(st, ev_out_done, 0));
     if (fs != GF_OK) {
         cudaStreamSynchronize(ctx->copy_in);
         cudaStreamSynchronize(ctx->copy_out);
+        for (int c = 0; c < nchunk; c++) cudaStreamSynchronize(ctx->pipe_st[c]);
         cudaStreamSynchronize(st);
         return fs;
     }
