@@ -211,3 +211,32 @@ def test_argument_errors_launch_nothing():
                 dict(ring_dist=95, annulus=2), dict(length=0.0), dict(Lambda=0.0), dict(t_high=float("nan"))):
         with pytest.raises(GuidefillError):
             ctx.detect_splines(img, lab, **bad)
+
+
+@pytest.mark.parametrize("seed", [100, 102])
+def test_detected_guidance_through_the_fill(seed):
+    # the paper's automatic pipeline end to end: splines detected on the frame,
+    # their guide field, the fill; each side from its own detection (Lambda = 1e-5
+    # saturates every weight to 1, so the two guide fields agree exactly)
+    import torch
+
+    import paper_1611_05319_gb300 as gf
+    from _gpu import assert_parity, oracle_fill
+    f = configs.batch_frame(seed, poison=True, H=270, W=480)
+    img, lab = f["rgb"], f["labels"]
+    o = oracle.detect_splines(img, lab)
+    n = o["count"]
+    go = oracle.guidance(lab, 2 * np.arange(n + 1, dtype=np.int32), o["pts"].reshape(-1, 2), eta=3.0,
+                         weight=o["weight"])
+    assert ((np.abs(go).sum(-1) > 0) & (lab == 1)).sum() > 1000
+    ctx = gf.context(0)
+    gg, det = ctx.guidance_auto_batched([torch.from_numpy(img).cuda()], [torch.from_numpy(lab).cuda()], eta=3.0)
+    assert det[0].count() == n
+    gg = gg[0]
+    np.testing.assert_array_equal(gg.cpu().numpy(), go)
+    r = ctx.fill(torch.from_numpy(synth.to_rgba(img)).cuda(), torch.from_numpy(lab).cuda(), gg, enter=True, stall=True)
+    torch.cuda.synchronize()
+    g = dict(u=r.rgba.cpu().numpy(), shell=r.shell.cpu().numpy(), enter=r.enter.cpu().numpy(), stats=r.stats(),
+             stall_steps=r.stall_steps())
+    ref = oracle_fill(img, lab, go, eps=3.0, mu=50.0, c=0.05)
+    assert_parity(ref, g, lab)
