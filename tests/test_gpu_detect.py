@@ -240,3 +240,20 @@ def test_detected_guidance_through_the_fill(seed):
              stall_steps=r.stall_steps())
     ref = oracle_fill(img, lab, go, eps=3.0, mu=50.0, c=0.05)
     assert_parity(ref, g, lab)
+
+
+def test_bench_launch_64_frames_sampled():
+    # the launch the benchmark times: all 64 frames of the 1920x1080 batch in one
+    # call; two frames checked in full against the oracle, every frame's count,
+    # offsets and base order checked for validity
+    fr = [configs.batch_frame(100 + i, poison=False) for i in range(64)]
+    gb = _gpu_detect_batched([f["rgb"] for f in fr], [f["labels"] for f in fr])
+    for i in (7, 41):
+        _assert_detect_parity(oracle.detect_splines(fr[i]["rgb"], fr[i]["labels"], debug=True), gb[i])
+    for f, g in zip(fr, gb):
+        assert g["status"] == 0 and g["count"] > 0
+        assert (np.diff(g["base"]) > 0).all()  # raster order, no duplicates
+        lab = f["labels"].reshape(-1)
+        assert (lab[g["base"]] == 0).all()  # bases are known pixels
+        v = g["pts"][:, 1] - g["pts"][:, 0]
+        np.testing.assert_allclose(np.hypot(v[:, 0], v[:, 1]), 48.0, rtol=1e-5)
