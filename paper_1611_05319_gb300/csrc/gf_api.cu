@@ -1095,7 +1095,14 @@ gf_status gf_detect_splines_batched(gf_ctx *ctx, int n, const gf_detect_frame *f
     CK(cudaGetLastError());
     detect_classify_kernel<<<(unsigned)((tiles + 255) / 256), 256, 0, st>>>(da);
     CK(cudaGetLastError());
-    detect_dist_kernel<<<g_dist, DET_THREADS, sm_dist, st>>>(da);
+    if (da.cap <= DET_WARP_DIST_MAX_CAP) {
+        int per_sm_w = 0;
+        CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_w, detect_dist_warp_kernel, DET_THREADS, 0));
+        const unsigned g_w = (unsigned)std::min<int64_t>((tiles + 7) / 8, (int64_t)std::max(per_sm_w, 1) * ctx->sm_count);
+        detect_dist_warp_kernel<<<g_w, DET_THREADS, 0, st>>>(da);
+    } else {
+        detect_dist_kernel<<<g_dist, DET_THREADS, sm_dist, st>>>(da);
+    }
     CK(cudaGetLastError());
     CK(launch_detect_tensor(rS, g_tensor, sm_tensor, st, da));
     detect_union_kernel<<<g_list, DET_THREADS, 0, st>>>(da);

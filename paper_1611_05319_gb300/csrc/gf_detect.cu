@@ -266,6 +266,125 @@ __global__ void __launch_bounds__(DET_THREADS) detect_dist_kernel(const __grid_c
     }
 }
 
+// Warp-per-tile form of the distance kernel for cap <= 31, where the window is
+// at most 94 rows of 3 mask words: lane l holds window rows l, l + 32, l + 64 of
+// both masks in registers, a dilation step takes the rows above and below from
+// the neighbouring lanes by shuffles (rows past the window stay part of the
+// domain: they start empty and hold no original bits, so every pixel still
+// reads the OR of the original bits within its box), and the lane whose row is
+// tile row y counts, in bit-sliced 6-bit counters, the steps at which each of
+// its 32 pixels is not yet covered: that count is the distance (cap + 1 when
+// never covered).  No block barriers; eight tiles per CTA at once.
+constexpr int DW_SLOTS = 3;  // window rows per lane
+
+__device__ __forceinline__ uint32_t det_sel3(int s, uint32_t a0, uint32_t a1, uint32_t a2)
+{
+    return s == 0 ? a0 : (s == 1 ? a1 : a2);
+}
+
+// one 3x3-box dilation step of a window held as m[slot][word] (row = lane + 32 slot)
+__device__ __forceinline__ void det_dilate_warp(uint32_t (&m)[DW_SLOTS][3], int lane)
+{
+    uint32_t up[DW_SLOTS][3], dn[DW_SLOTS][3];
+#pragma unroll
+    for (int s = 0; s < DW_SLOTS; s++)
+#pragma unroll
+        for (int w = 0; w < 3; w++) {
+            const uint32_t u = __shfl_up_sync(0xffffffffu, m[s][w], 1);
+            const uint32_t uw = __shfl_sync(0xffffffffu, s > 0 ? m[s > 0 ? s - 1 : 0][w] : 0u, 31);
+            up[s][w] = lane == 0 ? (s > 0 ? uw : 0u) : u;
+            const uint32_t d = __shfl_down_sync(0xffffffffu, m[s][w], 1);
+            const uint32_t dw = __shfl_sync(0xffffffffu, s + 1 < DW_SLOTS ? m[s + 1 < DW_SLOTS ? s + 1 : s][w] : 0u, 0);
+            dn[s][w] = lane == 31 ? (s + 1 < DW_SLOTS ? dw : 0u) : d;
+        }
+#pragma unroll
+    for (int s = 0; s < DW_SLOTS; s++) {
+        // the three rows' OR first (vertical step), then the horizontal step on it
+        const uint32_t v0 = up[s][0] | m[s][0] | dn[s][0];
+        const uint32_t v1 = up[s][1] | m[s][1] | dn[s][1];
+        const uint32_t v2 = up[s][2] | m[s][2] | dn[s][2];
+        m[s][0] = v0 | (v0 << 1) | (v0 >> 1) | (v1 << 31);
+        m[s][1] = v1 | (v1 << 1) | (v1 >> 1) | (v0 >> 31) | (v2 << 31);
+        m[s][2] = v2 | (v2 << 1) | (v2 >> 1) | (v1 >> 31);
+    }
+}
+
+__global__ void __launch_bounds__(DET_THREADS) detect_dist_warp_kernel(const __grid_constant__ DetectArgs a)
+{
+    const int lane = threadIdx.x & 31;
+    const int nwarps = gridDim.x * (DET_THREADS / 32);
+    const int nslow = __ldcg(a.slow_count);
+    const int cap = a.cap, L = DT + 2 * cap, far = cap + 1, kn = a.dR - 1;
+    // tile row y of this lane: window row cap + y == lane (mod 32), in slot ts
+    const int ty = (lane - cap) & 31, ts = (cap + ty) >> 5;
+    for (int it = blockIdx.x * (DET_THREADS / 32) + (threadIdx.x >> 5); it < nslow; it += nwarps) {
+        const int gt = __ldcg(&a.slow_list[it]);
+        const int f = det_frame_of(a.tile_offset, a.n_frames, gt);
+        const DetectFrameDev &F = a.frames[f];
+        const int t = gt - __ldg(&a.tile_offset[f]);
+        const int tx = t % F.NBX;
+        const int x0 = tx * DT, y0 = (t / F.NBX) * DT;
+        uint32_t h[DW_SLOTS][3], nk[DW_SLOTS][3];
+        bool anyh = false;
+#pragma unroll
+        for (int s = 0; s < DW_SLOTS; s++) {
+            const int r = lane + 32 * s, Y = y0 - cap + r;
+#pragma unroll
+            for (int w = 0; w < 3; w++) {
+                const int k = tx - 1 + w;
+                uint2 v = make_uint2(0u, 0u);
+                if (r < L && Y >= 0 && Y < F.H && k >= 0 && k < F.NWF) v = __ldg(&F.masks[(size_t)Y * F.NWF + k]);
+                h[s][w] = v.x;
+                nk[s][w] = v.y;
+                anyh = anyh || v.x != 0u;
+            }
+        }
+        const uint32_t nk_orig = det_sel3(ts, nk[0][1], nk[1][1], nk[2][1]);
+        uint32_t cnt[6] = {0u, 0u, 0u, 0u, 0u, 0u};
+        uint32_t nkcov = 0xffffffffu;
+        if (__any_sync(0xffffffffu, anyh)) {
+            for (int k = 0;; k++) {
+                const uint32_t cov = det_sel3(ts, h[0][1], h[1][1], h[2][1]);
+                uint32_t carry = ~cov;  // pixels not covered at step k
+#pragma unroll
+                for (int b = 0; b < 6; b++) {
+                    const uint32_t c2 = cnt[b] & carry;
+                    cnt[b] ^= carry;
+                    carry = c2;
+                }
+                if (k == kn) nkcov = det_sel3(ts, nk[0][1], nk[1][1], nk[2][1]);
+                if (k == cap) break;
+                if (__all_sync(0xffffffffu, cov == 0xffffffffu) && k >= kn) break;
+                det_dilate_warp(h, lane);
+                if (k < kn) det_dilate_warp(nk, lane);
+            }
+        } else {
+#pragma unroll
+            for (int b = 0; b < 6; b++) cnt[b] = ((far >> b) & 1) ? 0xffffffffu : 0u;
+        }
+        // the tile's rows, one at a time, from the lane holding each (coalesced writes)
+        bool ann = false;
+        for (int y = 0; y < DT; y++) {
+            const int o = (cap + y) & 31;
+            int d = 0;
+#pragma unroll
+            for (int b = 0; b < 6; b++) d |= (int)((__shfl_sync(0xffffffffu, cnt[b], o) >> lane) & 1u) << b;
+            const uint32_t nkc = __shfl_sync(0xffffffffu, nkcov, o), nko = __shfl_sync(0xffffffffu, nk_orig, o);
+            const int Y = y0 + y, X = x0 + lane;
+            if (Y >= F.H || X >= F.W) continue;
+            const bool known = !((nko >> lane) & 1u);
+            const uint8_t ring = (known && d == a.dR && !((nkc >> lane) & 1u)) ? 1 : 0;
+            F.dist[(size_t)Y * F.W + X] = make_uchar2((uint8_t)d, ring);
+            const int dd = d - a.dR;
+            if (known && dd <= a.annulus && -dd <= a.annulus) ann = true;
+        }
+        if (__any_sync(0xffffffffu, ann) && lane == 0) {
+            F.act_t[t] = 1;
+            a.active_list[atomicAdd(a.active_count, 1)] = gt;
+        }
+    }
+}
+
 // ---------------------------------------------------------------------------
 // tensor, suppression, thresholds, ring candidates
 

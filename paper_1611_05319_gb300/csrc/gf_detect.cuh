@@ -100,6 +100,8 @@ __global__ void upload_detect_kernel(const __grid_constant__ DetectChunk c);
 __global__ void detect_pack_kernel(const __grid_constant__ DetectArgs a, int total_words);
 __global__ void detect_classify_kernel(const __grid_constant__ DetectArgs a);
 __global__ void detect_dist_kernel(const __grid_constant__ DetectArgs a);
+__global__ void detect_dist_warp_kernel(const __grid_constant__ DetectArgs a);  // cap <= 31
+constexpr int DET_WARP_DIST_MAX_CAP = 31;
 template <int RS>
 __global__ void detect_tensor_kernel(const __grid_constant__ DetectArgs a);
 // the instantiation for radius rS (1..DET_MAX_RS), and its launch
