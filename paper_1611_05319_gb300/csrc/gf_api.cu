@@ -491,7 +491,7 @@ static gf_status enqueue_fill(gf_ctx *ctx, int n, const gf_frame *frames, const 
         d.init_count = (int32_t *)(A + off_icnt) + 2 * i;
         hd[i] = d;
         hcta[i] = (int32_t)ctas;
-        ctas += (int64_t)d.TH * ((f.W + 255) / 256);
+        ctas += (int64_t)init_ctas(d.TH, f.W);
     }
     hcta[n] = (int32_t)ctas;
     if (ctas >= INT32_MAX) return GF_ERR_ARG;

@@ -52,13 +52,16 @@ __shared__ float4 g_stab[MAX_SAMPLES];
 // ---------------------------------------------------------------------------
 // init
 // ---------------------------------------------------------------------------
-// CTA = 256 threads = one strip of 8 rows x 256 columns (32 tiles) of a frame.
+// CTA = 256 threads = a band of INIT_STRIPS strips of 8 rows x 256 columns (32
+// tiles each) of a frame: the frame lookup and the labels of the whole band are
+// loaded once, then the strips are processed from shared memory.
 
 __global__ void __launch_bounds__(256) init_kernel(const __grid_constant__ InitArgs a)
 {
-    // labels of rows y0-1 .. y0+8, columns x0-16 .. x0+271 (0xff outside the image);
-    // column x of the strip sits at index x - x0 + 16
-    __shared__ __align__(16) uint8_t lab_s[10][288];
+    // labels of rows yb-1 .. yb+8*INIT_STRIPS, columns x0-16 .. x0+271 (0xff outside
+    // the image); column x sits at index x - x0 + 16, row y at y - yb + 1
+    constexpr int LR = TILE * INIT_STRIPS + 2;
+    __shared__ __align__(16) uint8_t lab_s[LR][288];
     __shared__ __align__(16) int32_t out_s[TILE][256];  // state words of the strip
     int b = blockIdx.x;
     int lo = 0, hi = a.n_frames;  // frame f with cta_offset[f] <= b < cta_offset[f+1]
@@ -70,26 +73,26 @@ __global__ void __launch_bounds__(256) init_kernel(const __grid_constant__ InitA
     const int H = F.H, W = F.W;
     const int strips = (W + 255) >> 8;
     const int local = b - __ldg(&a.cta_offset[lo]);
-    const int ty = local / strips;
-    const int x0 = (local - ty * strips) * 256;
-    const int y0 = ty * TILE;
+    const int band = local / strips;
+    const int x0 = (local - band * strips) * 256;
+    const int yb = band * TILE * INIT_STRIPS;
     const int t = threadIdx.x;
     // 16-byte label loads and state-word stores when every row starts on a 16-byte boundary
     const bool vec = (W & 15) == 0 && (reinterpret_cast<uintptr_t>(F.labels) & 15u) == 0 &&
                      (reinterpret_cast<uintptr_t>(F.shell) & 15u) == 0;
 
     if (vec) {
-        for (int e = t; e < 10 * 18; e += 256) {
+        for (int e = t; e < LR * 18; e += 256) {
             const int r = e / 18, c = e - r * 18;
-            const int y = y0 - 1 + r, x = x0 - 16 + 16 * c;
+            const int y = yb - 1 + r, x = x0 - 16 + 16 * c;
             uint4 v = make_uint4(0xffffffffu, 0xffffffffu, 0xffffffffu, 0xffffffffu);
             if (y >= 0 && y < H && x >= 0 && x < W) v = __ldg(reinterpret_cast<const uint4 *>(F.labels + (size_t)y * W + x));
             *reinterpret_cast<uint4 *>(&lab_s[r][16 * c]) = v;
         }
     } else {
-        for (int e = t; e < 10 * 258; e += 256) {
+        for (int e = t; e < LR * 258; e += 256) {
             const int r = e / 258, c = e - r * 258;
-            const int y = y0 - 1 + r, x = x0 - 1 + c;
+            const int y = yb - 1 + r, x = x0 - 1 + c;
             uint8_t v = 0xff;
             if (y >= 0 && y < H && x >= 0 && x < W) v = __ldg(&F.labels[(size_t)y * W + x]);
             lab_s[r][c + 15] = v;
@@ -101,12 +104,17 @@ __global__ void __launch_bounds__(256) init_kernel(const __grid_constant__ InitA
     const int lane = t & 31;
     const bool data = (a.flags & GF_FLAG_DATA) != 0;
     int gcount = 0;  // data term: hole pixels of this warp's columns with g != 0
+    for (int sub = 0; sub < INIT_STRIPS; sub++) {
+    const int ty = band * INIT_STRIPS + sub;  // tile row of the strip
+    const int y0 = ty * TILE;
+    if (y0 >= H) break;  // CTA-uniform
+    const int lr = TILE * sub;                // label row of the strip's row -1
     unsigned long long Um[4] = {0, 0, 0, 0}, Qm[4] = {0, 0, 0, 0};
 #pragma unroll
     for (int r = 0; r < TILE; r++) {
         int y = y0 + r;
         bool in = (y < H) && (x < W);
-        uint8_t l = in ? lab_s[r + 1][t + 16] : 0xff;
+        uint8_t l = in ? lab_s[lr + r + 1][t + 16] : 0xff;
         bool hole = in && l == 1;
         bool front = false;
         if (hole) {
@@ -114,7 +122,7 @@ __global__ void __launch_bounds__(256) init_kernel(const __grid_constant__ InitA
             for (int dy = 0; dy < 3; dy++)
 #pragma unroll
                 for (int dx = 0; dx < 3; dx++)
-                    if (!(dx == 1 && dy == 1) && lab_s[r + dy][t + 15 + dx] == 0) front = true;
+                    if (!(dx == 1 && dy == 1) && lab_s[lr + r + dy][t + 15 + dx] == 0) front = true;
         }
         const int32_t sw = (l == 0) ? SH_KNOWN : (l == 1 ? SH_UNFILLED : SH_BYST);
         if (vec) out_s[r][t] = sw;
@@ -144,8 +152,8 @@ __global__ void __launch_bounds__(256) init_kernel(const __grid_constant__ InitA
             if (y < H && x < W)
                 *reinterpret_cast<int4 *>(F.shell + (size_t)y * W + x) = *reinterpret_cast<const int4 *>(&out_s[r][4 * c4]);
         }
+        __syncthreads();  // out_s is rewritten by the next strip
     }
-    if (data && lane == 0 && gcount) atomicAdd(F.gleft, gcount);
     const int warp = t >> 5;
     bool has_front = false;
     int tile = 0, nq = 0;
@@ -178,6 +186,8 @@ __global__ void __launch_bounds__(256) init_kernel(const __grid_constant__ InitA
         b0 = __shfl_sync(FULL, b0, 0);
         if (has_front) F.init_list[b0 + __popc(bm & ((1u << lane) - 1u))] = tile;
     }
+    }
+    if (data && lane == 0 && gcount) atomicAdd(F.gleft, gcount);
 }
 
 __global__ void upload_frames_kernel(const __grid_constant__ FrameChunk c)

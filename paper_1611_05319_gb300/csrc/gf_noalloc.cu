@@ -200,7 +200,7 @@ extern "C" gf_status gf_fill_noalloc(const gf_frame *f, const gf_params *p, gf_s
     ch.last_chunk = 1;
     ch.frames[0] = d;
     ch.cta[0] = 0;
-    ch.cta[1] = TH * ((f->W + 255) / 256);
+    ch.cta[1] = init_ctas(TH, f->W);
 
     FillParams fp;
     memset(&fp, 0, sizeof(fp));
