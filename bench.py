@@ -46,10 +46,10 @@ SEED0, NFRAMES = 100, 64
 # roofline's traffic is reported as null.
 FILL_TRAFFIC = {
     "sources": {
-        "paper_1611_05319_gb300/csrc/gf_fill.cu": "3b841c33bb2aa72fd78577e48b1c364fe7cadf251d0ec25ccc867249afc0171f",
-        "paper_1611_05319_gb300/csrc/gf_internal.cuh": "7841dc110fb930f2584a863f024a2235eaac23e465987c13fb8818d1b852169d",
+        "paper_1611_05319_gb300/csrc/gf_fill.cu": "6388e7e478e05f0e2e432b3152802ea6bdd3fd45a8be07da001e8ac82f37a04e",
+        "paper_1611_05319_gb300/csrc/gf_internal.cuh": "f78a44b9ab487dd672ac86df35df35e2f7986e3d9fff779de3db33fb1a304ce4",
     },
-    "bytes_per_filled_px": (36.391936e6 + 0.742656e6) / 534164,
+    "bytes_per_filled_px": (36.3904e6 + 0.653568e6) / 534164,
 }
 
 
