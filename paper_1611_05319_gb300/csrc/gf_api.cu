@@ -1322,7 +1322,7 @@ gf_status gf_fill_batched_host(gf_ctx *ctx, int n, const int32_t *H, const int32
     // scratch of their own) as soon as its inputs have landed, so chunks whose
     // frames have long shell chains overlap the next chunks instead of delaying
     // them.  `copy_out` only joins the chunks' streams before `stream` continues.
-    const int nchunk = std::min(n, 8);
+    const int nchunk = std::min(n, 16);
     // frames are dealt to the chunks round-robin (position q of the pipeline order
     // holds frame perm[q])
     std::vector<int> perm;
@@ -1387,7 +1387,7 @@ gf_status gf_fill_batched_host(gf_ctx *ctx, int n, const int32_t *H, const int32
     }
     // Unless a launch shape was set, a chunk's frames get the largest cluster size at
     // which every one of them has its own cluster and two chunks fit on the SMs at
-    // once (4 CTAs for 8 frames on 152 SMs).  No split schedule: its second stream
+    // once (16 CTAs for 4 frames on 152 SMs).  No split schedule: its second stream
     // and events belong to the context.
     const int save_cs = ctx->cluster_size, save_nc = ctx->n_clusters;
     const int save_sm = ctx->split_m, save_scs = ctx->split_cs, save_snc = ctx->split_nc;
