@@ -257,11 +257,11 @@ def main():
         b.record(stream)
 
     def step(events=None):
-        _lib.check(L.gf_guidance_batched(ctx._h, n, sf, C.c_float(3.0), sptr), "guidance")
+        # guide fields from the splines (built beside the fill's preparation) + the batched fill
         e0 = C.c_void_p(events[0].cuda_event) if events else None
         e1 = C.c_void_p(events[1].cuda_event) if events else None
-        _lib.check(L.gf_fill_batched_ex(ctx._h, n, fr, C.byref(prm), C.c_void_p(stats.data_ptr()), sptr, e0, e1),
-                   "fill", ctx._h)
+        _lib.check(L.gf_fill_batched_splines(ctx._h, n, fr, sf, C.c_float(3.0), C.byref(prm),
+                                             C.c_void_p(stats.data_ptr()), sptr, e0, e1), "guided fill", ctx._h)
 
     # autotune the launch shape on this batch (outside the timed region)
     step()

@@ -226,6 +226,20 @@ gf_status gf_guidance_batched(gf_ctx *ctx, int n, const gf_spline_frame *frames,
                               void *stream);
 
 /*
+ * Guide fields from polylines and the batched fill in one call: the same results
+ * as gf_guidance_batched(splines) followed by gf_fill_batched_ex(frames).  The
+ * guide fields are built on the context's second stream while the fill's
+ * preparation (descriptors, init pass, frame order), which does not read them,
+ * runs on `stream`; the fill kernel starts once both are done.  (With
+ * GF_FLAG_DATA the init pass reads the guide field, so the two run one after the
+ * other.)  splines[i] must describe frame i: the same H, W, labels and guide
+ * pointers.  event_fill_start / event_fill_end as in gf_fill_batched_ex.
+ */
+gf_status gf_fill_batched_splines(gf_ctx *ctx, int n, const gf_frame *frames, const gf_spline_frame *splines,
+                                  float eta, const gf_params *params, gf_stats *dev_stats, void *stream,
+                                  void *event_fill_start, void *event_fill_end);
+
+/*
  * Automatic spline detection (Section 3.3).  A ring R of known pixels at
  * Chebyshev distance ring_dist from the hole D_h (labels == 1), with no hole or
  * bystander pixel nearer; Canny edge detection on the annulus of known pixels

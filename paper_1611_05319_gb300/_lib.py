@@ -27,7 +27,7 @@ EXPORTS = ["gf_create", "gf_destroy", "gf_status_string", "gf_last_cuda_error", 
            "gf_fill_batched", "gf_fill_batched_ex", "gf_fill_batched_host", "gf_guidance_from_splines", "gf_guidance_batched",
            "gf_set_launch_config", "gf_get_last_launch", "gf_max_active_clusters", "gf_fill_backward",
            "gf_guide_from_angle", "gf_autotune", "gf_fill_noalloc", "gf_set_split", "gf_get_last_split",
-           "gf_detect_splines", "gf_detect_splines_batched"]
+           "gf_detect_splines", "gf_detect_splines_batched", "gf_fill_batched_splines"]
 
 
 class Frame(C.Structure):
@@ -127,6 +127,9 @@ def lib() -> C.CDLL:
         L.gf_set_split.restype = C.c_int
         L.gf_get_last_split.argtypes = [P, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int)]
         L.gf_get_last_split.restype = C.c_int
+        L.gf_fill_batched_splines.argtypes = [P, C.c_int, C.POINTER(Frame), C.POINTER(SplineFrame), C.c_float,
+                                              C.POINTER(Params), P, P, P, P]
+        L.gf_fill_batched_splines.restype = C.c_int
         L.gf_detect_splines.argtypes = [P, C.POINTER(DetectFrame), C.POINTER(DetectParams), P]
         L.gf_detect_splines.restype = C.c_int
         L.gf_detect_splines_batched.argtypes = [P, C.c_int, C.POINTER(DetectFrame), C.POINTER(DetectParams), P]

@@ -44,6 +44,7 @@ struct gf_ctx {
     int last_split_m = 0, last_split_cs = 0, last_split_nc = 0;
     cudaStream_t aux = nullptr;                   // the second launch's stream
     cudaEvent_t fork_ev = nullptr, join_ev = nullptr;
+    cudaEvent_t guide_ev = nullptr;               // guide field done (gf_fill_batched_splines)
     // host-buffer path: copy streams, the events of its chunk pipeline, and per
     // chunk a stream and scratch for its guide field and fill (chunks overlap)
     cudaStream_t copy_in = nullptr, copy_out = nullptr;
@@ -272,6 +273,7 @@ gf_status gf_create(gf_ctx **out, int device)
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&ctx->copy_out, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->fork_ev, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->join_ev, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->guide_ev, cudaEventDisableTiming);
     if (e != cudaSuccess) {
         ctx->last_cuda = (int)e;
         gf_destroy(ctx);
@@ -292,6 +294,7 @@ void gf_destroy(gf_ctx *ctx)
     for (cudaStream_t s : ctx->pipe_st) cudaStreamDestroy(s);
     if (ctx->fork_ev) cudaEventDestroy(ctx->fork_ev);
     if (ctx->join_ev) cudaEventDestroy(ctx->join_ev);
+    if (ctx->guide_ev) cudaEventDestroy(ctx->guide_ev);
     cudaDeviceSynchronize();
     drop_graphs(ctx, nullptr);
     if (ctx->arena.ptr) cudaFree(ctx->arena.ptr);
@@ -379,7 +382,8 @@ int gf_max_active_clusters(gf_ctx *ctx, float eps, int cluster_size)
 
 static gf_status enqueue_fill(gf_ctx *ctx, int n, const gf_frame *frames, const gf_params *prm,
                               gf_stats *dev_stats, cudaStream_t stream, cudaEvent_t ev0 = nullptr,
-                              cudaEvent_t ev1 = nullptr, bool allow_graph = true, DevBuf *scratch = nullptr)
+                              cudaEvent_t ev1 = nullptr, bool allow_graph = true, DevBuf *scratch = nullptr,
+                              cudaEvent_t wait_before_fill = nullptr)
 {
     DevBuf &arena = scratch ? *scratch : ctx->arena;
     // ---- layout of the scratch arena
@@ -538,6 +542,7 @@ static gf_status enqueue_fill(gf_ctx *ctx, int n, const gf_frame *frames, const 
     const bool graph = allow_graph && ctx->use_graph && stream != nullptr;
     if (graph && ctx->gexec && ctx->gexec_fill && ctx->gkey == key) {
         CK(cudaGraphLaunch(ctx->gexec, stream));
+        if (wait_before_fill) CK(cudaStreamWaitEvent(stream, wait_before_fill, 0));
         if (ev0) CK(cudaEventRecord(ev0, stream));
         CK(cudaGraphLaunch(ctx->gexec_fill, stream));
         if (ev1) CK(cudaEventRecord(ev1, stream));
@@ -634,6 +639,7 @@ static gf_status enqueue_fill(gf_ctx *ctx, int n, const gf_frame *frames, const 
     };
     if (!graph) {
         // ---- phase 2 directly
+        if (wait_before_fill) CK(cudaStreamWaitEvent(stream, wait_before_fill, 0));
         if (ev0) CK(cudaEventRecord(ev0, stream));
         CK(launch_phase2());
         if (ev1) CK(cudaEventRecord(ev1, stream));
@@ -657,6 +663,7 @@ static gf_status enqueue_fill(gf_ctx *ctx, int n, const gf_frame *frames, const 
     }
     ctx->gkey = key;
     CK(cudaGraphLaunch(ctx->gexec, stream));
+    if (wait_before_fill) CK(cudaStreamWaitEvent(stream, wait_before_fill, 0));
     if (ev0) CK(cudaEventRecord(ev0, stream));
     CK(cudaGraphLaunch(ctx->gexec_fill, stream));
     if (ev1) CK(cudaEventRecord(ev1, stream));
@@ -1121,6 +1128,50 @@ gf_status gf_detect_splines_batched(gf_ctx *ctx, int n, const gf_detect_frame *f
 gf_status gf_detect_splines(gf_ctx *ctx, const gf_detect_frame *frame, const gf_detect_params *params, void *stream)
 {
     return gf_detect_splines_batched(ctx, 1, frame, params, stream);
+}
+
+gf_status gf_fill_batched_splines(gf_ctx *ctx, int n, const gf_frame *frames, const gf_spline_frame *splines, float eta,
+                                  const gf_params *params, gf_stats *dev_stats, void *stream, void *event_fill_start,
+                                  void *event_fill_end)
+{
+    if (!ctx || n <= 0 || !frames || !splines || !dev_stats) return GF_ERR_ARG;
+    gf_status s = check_params(params);
+    if (s != GF_OK) return s;
+    for (int i = 0; i < n; i++) {
+        s = check_frame(&frames[i]);
+        if (s != GF_OK) return s;
+        const gf_spline_frame &g = splines[i];
+        if (g.H != frames[i].H || g.W != frames[i].W || g.labels != frames[i].labels || g.guide != frames[i].guide)
+            return GF_ERR_ARG;
+    }
+    cudaError_t e = cudaSetDevice(ctx->device);
+    if (e != cudaSuccess) return cuda_fail(ctx, e);
+    cudaStream_t st = (cudaStream_t)stream;
+    if (params->flags & GF_FLAG_DATA) {
+        // the init pass counts guided hole pixels: the guide field comes first
+        s = gf_guidance_batched(ctx, n, splines, eta, stream);
+        if (s != GF_OK) return s;
+        return enqueue_fill(ctx, n, frames, params, dev_stats, st, (cudaEvent_t)event_fill_start,
+                            (cudaEvent_t)event_fill_end);
+    }
+    // the guide field on the context's second stream, beside the fill's preparation
+    // (descriptors, init pass, frame order), which does not read it; the fill kernel
+    // waits for both
+    CK(cudaEventRecord(ctx->fork_ev, st));
+    CK(cudaStreamWaitEvent(ctx->aux, ctx->fork_ev, 0));
+    s = gf_guidance_batched(ctx, n, splines, eta, ctx->aux);
+    if (s != GF_OK) {
+        cudaStreamSynchronize(ctx->aux);
+        return s;
+    }
+    CK(cudaEventRecord(ctx->guide_ev, ctx->aux));
+    s = enqueue_fill(ctx, n, frames, params, dev_stats, st, (cudaEvent_t)event_fill_start, (cudaEvent_t)event_fill_end,
+                     true, nullptr, ctx->guide_ev);
+    if (s != GF_OK) {
+        CK(cudaStreamWaitEvent(st, ctx->guide_ev, 0));  // leave nothing of this call unjoined
+        return s;
+    }
+    return GF_OK;
 }
 
 gf_status gf_guide_from_angle(gf_ctx *ctx, int H, int W, const uint8_t *labels, const float *mag, const float *phi,

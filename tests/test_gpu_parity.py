@@ -414,3 +414,62 @@ def test_host_buffer_pipeline_many_frames_matches_device_path():
         assert np.array_equal(outs[i][sh >= 0], r.rgba.cpu().numpy()[sh >= 0]), i
         rs = r.stats()
         assert (st[i]["filled"], st[i]["shells"], st[i]["holes"]) == (rs["filled"], rs["shells"], rs["holes"]), i
+
+
+@pytest.mark.parametrize("data_term", [False, True])
+def test_fill_batched_splines_equals_guidance_then_fill(data_term):
+    """gf_fill_batched_splines builds the guide fields beside the fill's preparation;
+    the results equal the guide fields followed by the batched fill, bit for bit,
+    and the guide fields themselves equal gf_guidance_batched's."""
+    import ctypes as C
+
+    import torch
+
+    import paper_1611_05319_gb300 as gf
+    from paper_1611_05319_gb300 import _lib
+    from synth import configs, to_rgba
+    ctx = gf.context(0)
+    dev = torch.device("cuda", 0)
+    fr_ = [configs.batch_frame(300 + i, poison=True, H=270, W=480) for i in range(6)]
+    n = len(fr_)
+    labs = [torch.from_numpy(f["labels"]).to(dev) for f in fr_]
+    offs = [torch.from_numpy(f["splines"][0]).to(dev) for f in fr_]
+    pts = [torch.from_numpy(f["splines"][1]).to(dev) for f in fr_]
+    ref_g = ctx.guidance_batched(labs, [f["splines"][0] for f in fr_], [f["splines"][1] for f in fr_], 3.0)
+    ref = ctx.fill_batched([torch.from_numpy(to_rgba(f["rgb"])).to(dev) for f in fr_], labs, ref_g, eps=3.0, mu=50.0,
+                           c=0.05, data_term=data_term)
+    torch.cuda.synchronize()
+    imgs = [torch.from_numpy(to_rgba(f["rgb"])).to(dev) for f in fr_]
+    guides = [torch.full((f["labels"].shape[0], f["labels"].shape[1], 2), 7.0, dtype=torch.float32, device=dev)
+              for f in fr_]
+    shells = [torch.empty(f["labels"].shape, dtype=torch.int32, device=dev) for f in fr_]
+    stats = torch.zeros((n * _lib.STATS_BYTES,), dtype=torch.uint8, device=dev)
+    frames = (_lib.Frame * n)()
+    sfr = (_lib.SplineFrame * n)()
+    for i, f in enumerate(fr_):
+        H, W = f["labels"].shape
+        frames[i] = _lib.Frame(H, W, imgs[i].data_ptr(), labs[i].data_ptr(), guides[i].data_ptr(), imgs[i].data_ptr(),
+                               shells[i].data_ptr(), None, None)
+        sfr[i] = _lib.SplineFrame(H, W, labs[i].data_ptr(), offs[i].numel() - 1, pts[i].shape[0], offs[i].data_ptr(),
+                                  pts[i].data_ptr(), guides[i].data_ptr(), None)
+    prm = _lib.make_params(eps=3.0, mu=50.0, c=0.05, data_term=data_term)
+    L = _lib.lib()
+    sp = C.c_void_p(torch.cuda.current_stream().cuda_stream)
+    for _ in range(2):  # the second call replays the cached graphs
+        for im, f in zip(imgs, fr_):
+            im.copy_(torch.from_numpy(to_rgba(f["rgb"])).to(dev))
+        _lib.check(L.gf_fill_batched_splines(ctx._h, n, frames, sfr, C.c_float(3.0), C.byref(prm),
+                                             C.c_void_p(stats.data_ptr()), sp, None, None), "fill_batched_splines",
+                   ctx._h)
+        torch.cuda.synchronize()
+        st = np.frombuffer(stats.cpu().numpy().tobytes(), dtype=_lib.STATS_DTYPE)
+        for i, r in enumerate(ref):
+            lab = fr_[i]["labels"]
+            hole = lab == 1
+            assert np.array_equal(guides[i].cpu().numpy()[hole], ref_g[i].cpu().numpy()[hole]), i
+            sh = r.shell.cpu().numpy()
+            assert np.array_equal(shells[i].cpu().numpy(), sh), i
+            assert np.array_equal(imgs[i].cpu().numpy()[sh >= 0], r.rgba.cpu().numpy()[sh >= 0]), i
+            rs = r.stats()
+            assert (st[i]["filled"], st[i]["shells"], st[i]["data_switch"]) == \
+                (rs["filled"], rs["shells"], rs["data_switch"]), i
