@@ -55,6 +55,8 @@ def test_status_strings_and_argument_errors_without_gpu(built_lib):
     assert lib.gf_guidance_batched(None, 1, None, C.c_float(3.0), None) == -1
     lib.gf_detect_splines_batched.restype = C.c_int
     assert lib.gf_detect_splines_batched(None, 1, None, None, None) == -1
+    lib.gf_fill_batched_splines.restype = C.c_int
+    assert lib.gf_fill_batched_splines(None, 1, None, None, C.c_float(3.0), None, None, None, None, None) == -1
 
 
 def test_struct_layouts_match_header(tmp_path):
