@@ -101,6 +101,41 @@ static void drop_graphs(gf_ctx *ctx, cudaStream_t stream)
     ctx->gkey = 0;
 }
 
+// Puts back the context's launch settings (cluster size, cluster count, split
+// schedule) when a call that overrides them for its own launches returns, on
+// every path including the early returns of CK.
+struct LaunchSettingsGuard {
+    gf_ctx *ctx;
+    int cs, nc, sm, scs, snc;
+    explicit LaunchSettingsGuard(gf_ctx *c)
+        : ctx(c), cs(c->cluster_size), nc(c->n_clusters), sm(c->split_m), scs(c->split_cs), snc(c->split_nc)
+    {
+    }
+    ~LaunchSettingsGuard()
+    {
+        ctx->cluster_size = cs;
+        ctx->n_clusters = nc;
+        ctx->split_m = sm;
+        ctx->split_cs = scs;
+        ctx->split_nc = snc;
+    }
+    LaunchSettingsGuard(const LaunchSettingsGuard &) = delete;
+    LaunchSettingsGuard &operator=(const LaunchSettingsGuard &) = delete;
+};
+
+// Two timing events destroyed on every return path.
+struct EventPair {
+    cudaEvent_t a = nullptr, b = nullptr;
+    EventPair() = default;
+    ~EventPair()
+    {
+        if (a) cudaEventDestroy(a);
+        if (b) cudaEventDestroy(b);
+    }
+    EventPair(const EventPair &) = delete;
+    EventPair &operator=(const EventPair &) = delete;
+};
+
 static gf_status ensure(gf_ctx *ctx, DevBuf &b, size_t bytes)
 {
     if (b.bytes >= bytes) return GF_OK;
@@ -712,11 +747,11 @@ gf_status gf_autotune(gf_ctx *ctx, int n, const gf_frame *frames, const gf_param
     if (e != cudaSuccess) return cuda_fail(ctx, e);
     cudaStream_t st = (cudaStream_t)stream;
     if (trials <= 0) trials = 3;
-    const int save_cs = ctx->cluster_size, save_nc = ctx->n_clusters;
-    const int save_sm = ctx->split_m, save_scs = ctx->split_cs, save_snc = ctx->split_nc;
-    cudaEvent_t e0, e1;
-    CK(cudaEventCreate(&e0));
-    CK(cudaEventCreate(&e1));
+    LaunchSettingsGuard keep(ctx);
+    EventPair ev;
+    CK(cudaEventCreate(&ev.a));
+    CK(cudaEventCreate(&ev.b));
+    const cudaEvent_t e0 = ev.a, e1 = ev.b;
     // mean fill-kernel time of one schedule over `trials` runs (after a capture run)
     auto measure = [&](float *avg) -> gf_status {
         gf_status r = enqueue_fill(ctx, n, frames, params, dev_stats, st);  // warm-up / capture
@@ -780,13 +815,6 @@ gf_status gf_autotune(gf_ctx *ctx, int n, const gf_frame *frames, const gf_param
             }
         }
     }
-    ctx->cluster_size = save_cs;
-    ctx->n_clusters = save_nc;
-    ctx->split_m = save_sm;
-    ctx->split_cs = save_scs;
-    ctx->split_nc = save_snc;
-    cudaEventDestroy(e0);
-    cudaEventDestroy(e1);
     if (s != GF_OK) return s;
     if (best_cs == 0) return GF_ERR_UNSUPPORTED;
     const uint64_t tk = tune_key(n, frames, params);
@@ -1440,8 +1468,7 @@ gf_status gf_fill_batched_host(gf_ctx *ctx, int n, const int32_t *H, const int32
     // which every one of them has its own cluster and two chunks fit on the SMs at
     // once (16 CTAs for 4 frames on 152 SMs).  No split schedule: its second stream
     // and events belong to the context.
-    const int save_cs = ctx->cluster_size, save_nc = ctx->n_clusters;
-    const int save_sm = ctx->split_m, save_scs = ctx->split_cs, save_snc = ctx->split_nc;
+    LaunchSettingsGuard keep(ctx);
     ctx->split_m = ctx->split_cs = ctx->split_nc = 0;
     gf_status fs = GF_OK;
     for (int c = 0; c < nchunk && fs == GF_OK; c++) {
@@ -1455,7 +1482,7 @@ gf_status gf_fill_batched_host(gf_ctx *ctx, int n, const int32_t *H, const int32
             fs = guidance_impl(ctx, ctx->pipe_guide[c], (int)sfc.size(), sfc.data(), eta, cs_st);
             if (fs != GF_OK) break;
         }
-        if (save_cs == 0) {
+        if (keep.cs == 0) {
             int cs = 16;
             while (cs > 1 && 2 * cs * (q1 - q0) > ctx->sm_count) cs >>= 1;
             ctx->cluster_size = cs;
@@ -1463,8 +1490,8 @@ gf_status gf_fill_batched_host(gf_ctx *ctx, int n, const int32_t *H, const int32
         }
         fs = enqueue_fill(ctx, q1 - q0, fr.data() + q0, params, (gf_stats *)(A + o_st) + q0, cs_st, nullptr, nullptr,
                           false, &ctx->pipe_fill[c]);
-        ctx->cluster_size = save_cs;
-        ctx->n_clusters = save_nc;
+        ctx->cluster_size = keep.cs;
+        ctx->n_clusters = keep.nc;
         if (fs != GF_OK) break;
         // the chunk's outputs leave on its own stream, so a chunk with a long shell
         // chain holds back no other chunk's copies
@@ -1477,9 +1504,6 @@ gf_status gf_fill_batched_host(gf_ctx *ctx, int n, const int32_t *H, const int32
         CK(cudaEventRecord(ctx->pipe_ev[3 + 2 * c], cs_st));
         CK(cudaStreamWaitEvent(ctx->copy_out, ctx->pipe_ev[3 + 2 * c], 0));
     }
-    ctx->split_m = save_sm;
-    ctx->split_cs = save_scs;
-    ctx->split_nc = save_snc;
     CK(cudaEventRecord(ev_out_done, ctx->copy_out));
     CK(cudaStreamWaitEvent(st, ev_out_done, 0));
     if (fs != GF_OK) {
