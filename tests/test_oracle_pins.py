@@ -401,6 +401,83 @@ def test_stall_rule_band_across_image():
     assert np.isfinite(r["u"]).all()
 
 
+def _stall_band_failures():
+    """Runs the oracle on the hand-worked stall band (tests/golden/stall_band.json)
+    and returns the list of disagreements with the hand-worked values."""
+    gold = json.load(open(os.path.join(HERE, "golden", "stall_band.json")))
+    H, W = 24, 40
+    hole = np.zeros((H, W), bool)
+    hole[8:16, :] = True
+    lab = synth.labels_from(hole)
+    g = synth.const_guide(H, W, 0.0)
+    yy, xx = np.mgrid[0:H, 0:W].astype(np.float64)
+    u = np.stack([0.1 + xx / 50, 0.2 + yy / 30, 0.3 + (xx + 2 * yy) / 100], axis=2)
+    r = oracle.fill(u, lab, g, eps=3.0, mu=50.0, c=0.05)
+    bad = []
+    want = np.full((H, W), gold["shell_outside_hole"], np.int32)
+    for row, k in gold["shell_of_row"].items():
+        want[int(row), :] = k
+    if not np.array_equal(r["shell"], want):
+        bad.append(f"shell map differs at {(r['shell'] != want).sum()} pixels")
+    if r["stats"]["stalls"] != gold["stalls"] or r["stats"]["shells"] != gold["shells"]:
+        bad.append(f"stalls/shells {r['stats']['stalls']}/{r['stats']['shells']}")
+    if list(r["stall_steps"]) != [1] * gold["shells"]:
+        bad.append(f"stall steps {list(r['stall_steps'])}")
+
+    def from_offsets(x, y, offs, img):
+        # the weighted average written out from the hand-listed readable offsets
+        ws = [eval(e, {"sqrt": math.sqrt}) for _, _, e in offs]
+        return sum(w * img[y + m, x + n] for (n, m, _), w in zip(offs, ws)) / sum(ws)
+
+    for key, (x, y) in (("pixel_20_8_step0", (20, 8)), ("pixel_0_8_step0", (0, 8))):
+        exp = np.array(gold[key]["colour"])
+        if np.abs(from_offsets(x, y, gold[key]["readable_offsets"], u) - exp).max() > 1e-12:
+            bad.append(f"{key}: the listed offsets do not give the listed colour")
+        if np.abs(r["u"][y, x] - exp).max() > 1e-12:
+            bad.append(f"{key}: oracle {r['u'][y, x]} vs {exp}")
+    exp = np.array(gold["pixel_20_9_step1"]["colour"])
+    if np.abs(r["u"][9, 20] - exp).max() > 1e-12:
+        bad.append(f"pixel_20_9_step1: oracle {r['u'][9, 20]} vs {exp}")
+    return bad
+
+
+def test_stall_band_hand_worked():
+    """Reading 8 (stall rule) pinned by hand: the 24 x 40 band with g parallel to
+    it stalls at every step, fills one row from each edge per step, and fills
+    with the 1/|(n, m)|-weighted average of the readable lattice points."""
+    assert _stall_band_failures() == []
+
+
+def _mutant_oracle(tmp_path, edits):
+    """The oracle compiled from a copy of its source with `edits` applied
+    (each old text must occur in the source)."""
+    import ctypes as C
+    import subprocess
+    src = open(os.path.join(os.path.dirname(oracle.__file__), "guidefill_oracle.c")).read()
+    for old, new in edits:
+        assert old in src, old
+        src = src.replace(old, new)
+    c = tmp_path / "mutant.c"
+    so = tmp_path / "libmutant.so"
+    c.write_text(src)
+    subprocess.run(["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared", "-o",
+                    str(so), str(c), "-lm"], check=True)
+    lib = C.CDLL(str(so))
+    lib.oracle_fill.restype = C.c_int
+    lib.oracle_fill.argtypes = oracle.lib().oracle_fill.argtypes
+    return lib
+
+
+@pytest.mark.parametrize("name,edits", [
+    ("weights 1/|d|^2", [("/ sqrt((double)(n * n + m * m));", "/ (double)(n * n + m * m);")]),
+    ("rotated weights in the stall pass", [("    if (isotropic) return 0.0;\n", "")]),
+])
+def test_stall_band_catches_planted_mistakes(tmp_path, monkeypatch, name, edits):
+    """A slip in the stall rule's weights, planted in a copy of the oracle, fails the hand-worked band."""
+    monkeypatch.setattr(oracle, "_lib", _mutant_oracle(tmp_path, edits))
+    assert _stall_band_failures() != [], name
+
+
 # ----------------------------------------------------------------------------
 # Guide field from splines (Section 3.3)
 # ----------------------------------------------------------------------------
@@ -445,6 +522,35 @@ def test_guidance_tie_lowest_index():
     pts = np.array([[5, 10], [25, 10], [25, 14], [5, 14]], np.float32)
     g = oracle.guidance(lab, off, pts, eta=3.0)
     assert np.allclose(g[12, 15], [math.exp(-4 / 18), 0.0], atol=1e-7)
+
+
+def test_guidance_ties_report_the_other_choice():
+    """Near-ties of the nearest-segment choice and of the 3 eta cut are flagged
+    with the other choice's value (closed forms); decisions clear of a tie are
+    not, and their smallest gap is reported."""
+    H, W = 40, 40
+    lab = np.ones((H, W), np.uint8)
+    # two parallel segments 4 px apart (index 0 at y = 10 pointing +x, index 1 at
+    # y = 14 pointing -x): row 12 is equidistant; a corner polyline (5,30)-(20,30)-(20,35)
+    off = np.array([0, 2, 4, 7], np.int32)
+    pts = np.array([[5, 10], [25, 10], [25, 14], [5, 14], [5, 30], [20, 30], [20, 35]], np.float32)
+    r = oracle.guidance_ties(lab, off, pts, eta=3.0)
+    g, alt, tie = r["guide"], r["alt"], r["tie"]
+    e2 = math.exp(-4 / 18)
+    assert tie[12, 15] and np.allclose(g[12, 15], [e2, 0.0], atol=1e-7) and np.allclose(alt[12, 15], [-e2, 0.0],
+                                                                                         atol=1e-7)
+    assert not tie[11, 15] and np.array_equal(alt[11, 15], g[11, 15])
+    # outside the corner at (20, 30), on the bisector: both segments' nearest point is the vertex
+    d = math.hypot(2, 2)
+    e = math.exp(-d * d / 18)
+    assert tie[28, 22] and np.allclose(g[28, 22], [e, 0.0], atol=1e-7) and np.allclose(alt[28, 22], [0.0, e],
+                                                                                        atol=1e-7)
+    # d = 9 = 3 eta above the upper parallel segment (nothing else within 9 px): the cut is a tie
+    assert tie[1, 15] and np.allclose(g[1, 15], [math.exp(-81 / 18), 0.0], atol=1e-7)
+    assert np.array_equal(alt[1, 15], [0.0, 0.0])
+    assert not tie[2, 15] and not tie[0, 15] and np.array_equal(g[0, 15], [0.0, 0.0])
+    assert r["n_ties"] == int(tie.sum()) > 0
+    assert oracle.SEG_TIE_PX < r["min_gap"] < 0.5
 
 
 # ----------------------------------------------------------------------------
