@@ -85,7 +85,8 @@ def lib():
         _lib.oracle_fill.argtypes = [C.c_int, C.c_int, C.c_int, P, P, P, C.c_double, C.c_double,
                                      C.c_double, C.c_uint, C.c_float, C.c_int, P, P, P, P]
         _lib.oracle_guidance.restype = C.c_int
-        _lib.oracle_guidance.argtypes = [C.c_int, C.c_int, P, C.c_int, P, P, C.c_float, P, P]
+        _lib.oracle_guidance.argtypes = [C.c_int, C.c_int, P, C.c_int, P, P, C.c_float, P, P, P, P,
+                                         C.POINTER(C.c_double)]
         _lib.oracle_detect_splines.restype = C.c_int
         _lib.oracle_detect_splines.argtypes = [C.c_int, C.c_int, P, P, C.POINTER(DetParams), C.c_int, P, P, P,
                                                C.POINTER(DetDebug)]
@@ -144,17 +145,33 @@ def guidance(labels, offsets, pts, eta=3.0, H=None, W=None, weight=None):
     """Guide field from polylines (Section 3.3), float32 [H, W, 2]; zero outside
     the hole.  weight: optional float32 [n_splines], the magnitude |g_Gamma| of
     each spline's direction (1 when omitted)."""
+    return guidance_ties(labels, offsets, pts, eta, weight=weight)["guide"]
+
+
+SEG_TIE_PX = 1e-3  # width of the tie band of the nearest-segment and 3-eta decisions (px)
+
+
+def guidance_ties(labels, offsets, pts, eta=3.0, weight=None):
+    """Guide field (as ``guidance``) with its near-ties: dict(guide, alt, tie,
+    n_ties, min_gap).  Where ``tie`` is set the nearest-segment choice or the
+    3 eta cut is within SEG_TIE_PX px of a tie and ``alt`` holds the value of the
+    other choice (both are valid); ``min_gap`` is the smallest decision gap (px)
+    over the other hole pixels."""
     lab = np.ascontiguousarray(labels, np.uint8)
     H, W = lab.shape
     off = np.ascontiguousarray(offsets, np.int32)
     P = np.ascontiguousarray(pts, np.float32)
     g = np.zeros((H, W, 2), np.float32)
+    alt = np.zeros((H, W, 2), np.float32)
+    tie = np.zeros((H, W), np.uint8)
+    mg = C.c_double(0.0)
     w = None if weight is None else np.ascontiguousarray(weight, np.float32)
     assert w is None or w.shape == (len(off) - 1,)
-    rc = lib().oracle_guidance(H, W, _p(lab), len(off) - 1, _p(off), _p(P), _f32(eta), _p(w), _p(g))
-    if rc != 0:
+    rc = lib().oracle_guidance(H, W, _p(lab), len(off) - 1, _p(off), _p(P), _f32(eta), _p(w), _p(g), _p(alt),
+                               _p(tie), C.byref(mg))
+    if rc < 0:
         raise ValueError("oracle_guidance: bad arguments")
-    return g
+    return dict(guide=g, alt=alt, tie=tie.astype(bool), n_ties=int(rc), min_gap=mg.value)
 
 
 def alg_bytes(labels, guide, eps, shell, enter, ghost=True, tau=1e-5):

@@ -413,7 +413,12 @@ int oracle_fill(int H, int W, int C, double *u, const uint8_t *lab, const float 
  * g(x) = t * exp(-d^2 / (2 eta^2)) with t the segment's unit tangent, else 0.
  * The nearest-segment choice and the 3-eta cut are decided in FP32 with a
  * fixed expression (ties: lowest global segment index); the returned value is
- * computed in FP64 for the chosen segment and rounded once to FP32.
+ * computed in FP64 for the chosen segment and rounded once to FP32.  The paper
+ * fixes no rounding for this choice; the expression (with 1/|v|^2 formed once
+ * per segment) was chosen to be the one the CUDA sampler evaluates, so that
+ * both sides decide near-ties alike.  Where a decision is that close to a tie
+ * (two segments within SEG_TIE_PX, or d within SEG_TIE_PX of 3 eta) both
+ * choices are valid readings and the other choice's value is reported.
  * offsets[n+1], pts[P][2] as (x, y); guide [H][W][2] is written at hole
  * pixels only.  Zero-length segments are skipped.
  */
@@ -436,20 +441,70 @@ static float seg_dist2_f32(float px, float py, float ax, float ay, float bx, flo
     return d2;
 }
 
+/* FP64 value of the guide field at pixel (x, y) from segment bi: t = ((x - a).v)
+ * * (1/|v|^2) clamped to [0, 1], d^2 = |x - a - t v|^2, g = (v/|v|) *
+ * exp(-(d^2 * (1/(2 eta^2)))) * w, rounded once to FP32 (Section 3.3:
+ * g_Gamma e^(-d^2/(2 eta^2)) with |g_Gamma| = w the spline's coherence weight,
+ * 1 when no weights are given).  *dist receives the FP64 distance d. */
+static void seg_value(int n_splines, const int32_t *offsets, const float *pts, const float *weight, int bi,
+                      int x, int y, double k2, float *gx, float *gy, double *dist)
+{
+    int sb = 0;
+    while (sb + 1 < n_splines && offsets[sb + 1] <= bi) sb++;
+    double w = weight ? (double)weight[sb] : 1.0;
+    double ax = pts[2 * bi], ay = pts[2 * bi + 1];
+    double bx = pts[2 * bi + 2], by = pts[2 * bi + 3];
+    double vx = bx - ax, vy = by - ay;
+    double len = sqrt(vx * vx + vy * vy);
+    double inv_l2 = 1.0 / (len * len);
+    double wx = (double)x - ax, wy = (double)y - ay;
+    double t = (wx * vx + wy * vy) * inv_l2;
+    if (t < 0.0) t = 0.0;
+    if (t > 1.0) t = 1.0;
+    double qx = wx - t * vx, qy = wy - t * vy;
+    double d2 = qx * qx + qy * qy;
+    double e = exp(-(d2 * k2));
+    *gx = (float)(vx / len * e * w);
+    *gy = (float)(vy / len * e * w);
+    *dist = sqrt(d2);
+}
+
+/* Width of the band around a tie within which the nearest-segment choice and
+ * the 3 eta cut are left to rounding: two segments whose FP64 distances differ
+ * by less than this (in pixels), or a distance this close to 3 eta.  The FP32
+ * distance expression errs by about 7 * 2^-24 * |v| px (|v| the segment
+ * length), i.e. under 1e-4 px for segments up to 200 px. */
+#define SEG_TIE_PX 1e-3
+
+/*
+ * alt [H][W][2] (optional): where the pixel's decision is within SEG_TIE_PX of
+ * a tie, the value the other choice gives (the runner-up segment, or 0 / the
+ * nearest segment's value across the 3 eta cut); elsewhere the same value as
+ * guide.  Both are valid readings of "the nearest spline" there.
+ * tie [H][W] (optional): 1 where alt holds the other choice.
+ * min_gap (optional): the smallest decision gap (px) over the hole pixels that
+ * are not ties (> SEG_TIE_PX by construction; +inf when there is none).
+ * Returns the number of tie pixels, or -1 on bad arguments.
+ */
 int oracle_guidance(int H, int W, const uint8_t *lab, int n_splines, const int32_t *offsets,
-                    const float *pts, float eta, const float *weight, float *guide)
+                    const float *pts, float eta, const float *weight, float *guide, float *alt,
+                    uint8_t *tie, double *min_gap)
 {
     if (H <= 0 || W <= 0 || n_splines < 0 || !(eta > 0.0f)) return -1;
     float t3 = 3.0f * eta;
     float thr = t3 * t3;
     double k2 = 1.0 / (2.0 * (double)eta * (double)eta); /* 1/(2 eta^2) */
+    double cut = 3.0 * (double)eta;
+    int ties = 0;
+    double mg = INFINITY;
     for (int y = 0; y < H; y++)
         for (int x = 0; x < W; x++) {
             size_t p = (size_t)y * W + x;
+            if (tie) tie[p] = 0;
             if (lab[p] != LBL_HOLE) continue;
             float px = (float)x, py = (float)y;
-            float best = INFINITY;
-            int bi = -1;
+            float best = INFINITY, second = INFINITY;
+            int bi = -1, si = -1;
             for (int s = 0; s < n_splines; s++)
                 for (int i = offsets[s]; i + 1 < offsets[s + 1]; i++) {
                     float ax = pts[2 * i], ay = pts[2 * i + 1];
@@ -460,40 +515,61 @@ int oracle_guidance(int H, int W, const uint8_t *lab, int n_splines, const int32
                     if (!(l2 > 0.0f)) continue;
                     float d2 = seg_dist2_f32(px, py, ax, ay, bx, by);
                     if (d2 < best) {
+                        second = best;
+                        si = bi;
                         best = d2;
                         bi = i;
+                    } else if (d2 < second) {
+                        second = d2;
+                        si = i;
                     }
                 }
-            if (bi < 0 || !(best <= thr)) {
-                guide[2 * p] = 0.0f;
-                guide[2 * p + 1] = 0.0f;
-                continue;
+            float g0x = 0.0f, g0y = 0.0f, g1x = 0.0f, g1y = 0.0f;
+            double d_best = INFINITY, d_second = INFINITY;
+            if (bi >= 0) seg_value(n_splines, offsets, pts, weight, bi, x, y, k2, &g1x, &g1y, &d_best);
+            const int inside = bi >= 0 && best <= thr;
+            if (inside) {
+                g0x = g1x;
+                g0y = g1y;
             }
-            /* FP64 value for the chosen segment: t = ((x - a).v) * (1/|v|^2) clamped to
-             * [0, 1], d^2 = |x - a - t v|^2, g = (v/|v|) * exp(-(d^2 * (1/(2 eta^2)))) * w,
-             * rounded once to FP32 (Section 3.3: g_Gamma e^(-d^2/(2 eta^2)) with
-             * |g_Gamma| = w the spline's coherence weight). */
-            /* the spline holding segment bi, for its weight (the coherence factor of
-             * g_Gamma; 1 when no weights are given) */
-            int sb = 0;
-            while (offsets[sb + 1] <= bi) sb++;
-            double w = weight ? (double)weight[sb] : 1.0;
-            double ax = pts[2 * bi], ay = pts[2 * bi + 1];
-            double bx = pts[2 * bi + 2], by = pts[2 * bi + 3];
-            double vx = bx - ax, vy = by - ay;
-            double len = sqrt(vx * vx + vy * vy);
-            double inv_l2 = 1.0 / (len * len);
-            double wx = (double)x - ax, wy = (double)y - ay;
-            double t = (wx * vx + wy * vy) * inv_l2;
-            if (t < 0.0) t = 0.0;
-            if (t > 1.0) t = 1.0;
-            double qx = wx - t * vx, qy = wy - t * vy;
-            double d2 = qx * qx + qy * qy;
-            double e = exp(-(d2 * k2));
-            guide[2 * p] = (float)(vx / len * e * w);
-            guide[2 * p + 1] = (float)(vy / len * e * w);
+            guide[2 * p] = g0x;
+            guide[2 * p + 1] = g0y;
+            /* the decisions' gaps: runner-up segment, and the 3 eta cut */
+            float ax_ = g0x, ay_ = g0y;
+            double gap = INFINITY;
+            int is_tie = 0;
+            if (bi >= 0) {
+                double gc = fabs(d_best - cut);
+                if (gc < SEG_TIE_PX) {
+                    is_tie = 1;
+                    ax_ = inside ? 0.0f : g1x;
+                    ay_ = inside ? 0.0f : g1y;
+                } else if (gc < gap) {
+                    gap = gc;
+                }
+            }
+            if (inside && si >= 0) {
+                float sx, sy;
+                seg_value(n_splines, offsets, pts, weight, si, x, y, k2, &sx, &sy, &d_second);
+                double gs = fabs(d_second - d_best);
+                if (gs < SEG_TIE_PX) {
+                    is_tie = 1;
+                    ax_ = sx;
+                    ay_ = sy;
+                } else if (gs < gap) {
+                    gap = gs;
+                }
+            }
+            if (is_tie) ties++;
+            else if (gap < mg) mg = gap;
+            if (alt) {
+                alt[2 * p] = ax_;
+                alt[2 * p + 1] = ay_;
+            }
+            if (tie) tie[p] = (uint8_t)is_tie;
         }
-    return 0;
+    if (min_gap) *min_gap = mg;
+    return ties;
 }
 
 /* ---------------------------------------------------------------------- */

@@ -51,6 +51,21 @@ def assert_parity(o, g, labels, atol=COLOUR_ATOL, check_enter=True):
     return True
 
 
+def assert_guide_parity(ties, gg, labels):
+    """GPU guide field against oracle.guidance_ties: bit-exact wherever the
+    nearest-segment choice and the 3 eta cut are clear of a tie (the value is
+    unique there), and one of the two valid values at the near-ties.  Returns
+    the number of near-tie pixels."""
+    hole = labels == 1
+    g, alt, tie = ties["guide"], ties["alt"], ties["tie"]
+    clear = hole & ~tie
+    assert np.array_equal(g[clear], gg[clear]), _diff(g[clear], gg[clear])
+    t = hole & tie
+    ok = np.all(gg[t] == g[t], axis=-1) | np.all(gg[t] == alt[t], axis=-1)
+    assert ok.all(), f"{(~ok).sum()} near-tie pixels hold neither valid value"
+    return int(t.sum())
+
+
 def _diff(a, b):
     idx = np.argwhere(a != b)
     return f"{len(idx)} mismatches, first {idx[:5].tolist()}: {a[tuple(idx[0])] if len(idx) else ''} vs " \
@@ -66,3 +81,18 @@ def hole_blobs(H, W, seed, n=6, rmin=2, rmax=7, margin=0):
         r = rng.uniform(rmin, rmax)
         hole |= (xx - cx) ** 2 + (yy - cy) ** 2 <= r * r
     return hole
+
+
+def oracle_batch_job(args):
+    """Oracle side of one frame of the 64-frame batch, for a spawned worker:
+    the guide field with its near-ties from the frame's splines, and the fill of
+    the frame with the guide field the GPU built (its input; the guide fields
+    are compared separately).  Returns compact arrays."""
+    seed, gpu_guide = args
+    from synth import configs
+    f = configs.batch_frame(seed, poison=True)
+    ties = oracle.guidance_ties(f["labels"], *f["splines"], eta=3.0)
+    o = oracle.fill(rgba(f["rgb"]), f["labels"], gpu_guide, eps=3.0, mu=50.0, c=0.05)
+    filled = o["shell"] >= 0
+    return dict(seed=seed, shell=o["shell"], enter=o["enter"], u_filled=o["u"][filled], stats=o["stats"],
+                stall_steps=o["stall_steps"], ties={k: ties[k] for k in ("guide", "alt", "tie", "min_gap", "n_ties")})
