@@ -137,19 +137,21 @@ gf_status gf_fill(gf_ctx *ctx, const gf_frame *frame, const gf_params *params, g
 
 /*
  * gf_fill without any device allocation.  The paper has no counterpart: this
- * is for callers that cannot call cudaMalloc -- code enqueuing work while its
- * stream is being captured into a CUDA graph, hosts that own all device
- * memory, loops that must not allocate after start-up.  The library's scratch
- * is a fixed file-scope __device__ array (about 11 MB, held by every GPU that
- * loads the library until the process exits) instead of cudaMalloc memory, so:
+ * is for callers that cannot call cudaMalloc -- hosts that own all device
+ * memory and hand libraries none, loops that must not allocate (or risk an
+ * allocation failure) once they run.  The library's scratch is a fixed
+ * file-scope __device__ array (about 11 MB, held by every GPU that loads the
+ * library until the process exits) instead of cudaMalloc memory, so:
  *  - frames larger than 4096 x 4096 px or 4,194,304 px in total are rejected
  *    with GF_ERR_TOO_LARGE (nothing launched);
  *  - every call shares the array, which keeps the last call's contents (each
  *    call clears what must start at zero); calls that overlap on the GPU
  *    (unordered streams or host threads) race on it;
  *  - the first call on a device looks up the array's address and sets kernel
- *    attributes with that device current: make it before any stream capture.
- * Inputs and outputs as gf_fill; the current CUDA device is used; no context.
+ *    attributes with that device current: make it before any stream capture;
+ *    after a cudaDeviceReset of that device it must not be called again.
+ * Inputs, outputs and flags (GF_FLAG_DATA included) as gf_fill; the current
+ * CUDA device is used; no context.
  */
 gf_status gf_fill_noalloc(const gf_frame *frame, const gf_params *params, gf_stats *dev_stats,
                           void *stream);

@@ -1,12 +1,11 @@
 // gf_fill_noalloc: the fill of one frame with no device allocation.
 //
-// Some callers cannot call cudaMalloc: code that enqueues work while its stream
-// is being captured into a CUDA graph (an allocation there breaks the capture),
-// hosts that own every byte of device memory and hand libraries none, and
-// real-time loops that must not allocate (or risk an allocation failure) after
-// start-up.  This entry point runs the same kernels as gf_fill, but the
-// library's scratch lives in a fixed file-scope __device__ array instead of
-// memory from cudaMalloc.
+// Some callers cannot call cudaMalloc: hosts that own every byte of device
+// memory (a frame server or engine that sizes its pools at start-up) and hand
+// libraries none, and real-time loops that must not allocate, or risk an
+// allocation failure, once they run.  This entry point runs the same kernels
+// as gf_fill, but the library's scratch lives in a fixed file-scope __device__
+// array instead of memory from cudaMalloc.
 //
 // Limits: frames up to 4096 x 4096 px and 4,194,304 px in total; larger frames
 // are rejected with GF_ERR_TOO_LARGE before anything is launched.  The array
@@ -18,7 +17,9 @@
 //
 // The first call on each device looks up the array's device address and sets
 // the kernels' shared-memory and cluster attributes; make that first call
-// before starting any stream capture.
+// before starting any stream capture.  The address is kept for the rest of the
+// process: after a cudaDeviceReset of that device, do not call this entry point
+// again.
 
 #include <cuda_runtime.h>
 
@@ -103,6 +104,10 @@ cudaError_t setup_device(int dev)
 {
     std::lock_guard<std::mutex> lock(g_setup_mutex);
     if (g_scratch_addr[dev]) return cudaSuccess;
+    // an error left pending by the caller's own earlier work is reported, not
+    // cleared by the probes below
+    cudaError_t pending = cudaPeekAtLastError();
+    if (pending != cudaSuccess) return pending;
     void *ptr = nullptr;
     cudaError_t e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
     if (e != cudaSuccess) return e;
@@ -126,8 +131,8 @@ cudaError_t setup_device(int dev)
             cfg.attrs = at;
             cfg.numAttrs = 1;
             int n = 0;
-            if (cudaOccupancyMaxActiveClusters(&n, k, &cfg) == cudaSuccess && n > 0) best = cs;
-            cudaGetLastError();
+            if (cudaOccupancyMaxActiveClusters(&n, k, &cfg) != cudaSuccess) cudaGetLastError();
+            else if (n > 0) best = cs;
         }
         if (best == 0) return cudaErrorInvalidConfiguration;
         g_cluster[dev][i] = best;
@@ -143,7 +148,7 @@ extern "C" gf_status gf_fill_noalloc(const gf_frame *f, const gf_params *p, gf_s
     // ---- arguments (as gf_fill), then the size limit of the fixed scratch
     if (!f || !p || !dev_stats) return GF_ERR_ARG;
     if (!(p->eps >= 1.0f && p->eps <= 7.0f) || !(p->mu >= 0.0f) || !std::isfinite(p->mu)) return GF_ERR_ARG;
-    if (p->flags & ~(GF_FLAG_GHOST | GF_FLAG_SMART | GF_FLAG_RESCAN)) return GF_ERR_ARG;
+    if (p->flags & ~(GF_FLAG_GHOST | GF_FLAG_SMART | GF_FLAG_RESCAN | GF_FLAG_DATA)) return GF_ERR_ARG;
     if ((p->flags & GF_FLAG_SMART) && !(p->c >= 1e-6f && p->c < 1.0f)) return GF_ERR_ARG;
     if (!(p->snap_tau >= 0.0f && p->snap_tau < 0.01f) || p->max_shells < 0) return GF_ERR_ARG;
     if (f->H <= 0 || f->W <= 0) return GF_ERR_ARG;
@@ -239,7 +244,7 @@ extern "C" gf_status gf_fill_noalloc(const gf_frame *f, const gf_params *p, gf_s
     ia.cta_offset = (const int32_t *)(A + l.ctaoff);
     ia.n_frames = 1;
     ia.flags = p->flags;
-    init_kernel<<<(unsigned)ch.cta[1], 256, 0, st>>>(ia);
+    init_kernel<<<(unsigned)ch.cta[1], 32 * INIT_WARPS, 0, st>>>(ia);
     order_kernel<<<1, 256, 0, st>>>(fp.frames, 1, fp.frame_order, fp.frame_cursor);
     if (cudaGetLastError() != cudaSuccess) return GF_ERR_CUDA;
     cudaLaunchConfig_t cfg = {};
