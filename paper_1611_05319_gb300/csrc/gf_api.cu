@@ -638,7 +638,7 @@ static gf_status enqueue_fill(gf_ctx *ctx, int n, const gf_frame *frames, const 
         ia.cta_offset = (const int32_t *)(A + off_ctaoff);
         ia.n_frames = n;
         ia.flags = prm->flags;
-        init_kernel<<<(unsigned)ctas, 256, 0, stream>>>(ia);
+        init_kernel<<<(unsigned)ctas, 32 * INIT_WARPS, 0, stream>>>(ia);
         e = cudaGetLastError();
         if (e) break;
         order_kernel<<<1, 256, 0, stream>>>(fp.frames, n, fp.frame_order, fp.frame_cursor);

@@ -3,8 +3,8 @@
 // Kernels:
 //   init_kernel   one pass over every frame: state word per pixel (out_shell),
 //                 per 8x8 tile the bitmask of hole pixels (U) and of the initial
-//                 active boundary (Qw = d_active D^(0)_h, Notation) built with
-//                 warp ballots, per-frame hole count.
+//                 active boundary (Qw = d_active D^(0)_h, Notation) from bit
+//                 operations on the labels, per-frame hole count.
 //   order_kernel  sorts frames by hole size (largest first) into the work queue
 //                 (a split schedule gives its first frames to a second launch
 //                 with larger clusters, running beside the first).
@@ -52,142 +52,152 @@ __shared__ float4 g_stab[MAX_SAMPLES];
 // ---------------------------------------------------------------------------
 // init
 // ---------------------------------------------------------------------------
-// CTA = 256 threads = a band of INIT_STRIPS strips of 8 rows x 256 columns (32
-// tiles each) of a frame: the frame lookup and the labels of the whole band are
-// loaded once, then the strips are processed from shared memory.
+// One warp per strip of 8 pixel rows x 32 tiles (256 columns); lane l owns tile
+// column 32 s + l, i.e. 8 pixel columns, and holds the known and hole bits of its
+// columns (plus one column each side) for the strip's rows and the row above and
+// below.  The active boundary of D^(0)_h (hole pixels with a known 8-neighbour)
+// is then a few bit operations per row, the state words are written as two
+// 16-byte stores per row and lane, and each lane writes its tile's masks.
+// INIT_WARPS strips per CTA.
 
-__global__ void __launch_bounds__(256) init_kernel(const __grid_constant__ InitArgs a)
+__device__ __forceinline__ void init_label_row(const uint8_t *labels, int W, int H, int y, int x0, bool vec8,
+                                               uint32_t &kn, uint32_t &ho)
 {
-    // labels of rows yb-1 .. yb+8*INIT_STRIPS, columns x0-16 .. x0+271 (0xff outside
-    // the image); column x sits at index x - x0 + 16, row y at y - yb + 1
-    constexpr int LR = TILE * INIT_STRIPS + 2;
-    __shared__ __align__(16) uint8_t lab_s[LR][288];
-    __shared__ __align__(16) int32_t out_s[TILE][256];  // state words of the strip
-    int b = blockIdx.x;
+    // labels of columns x0 .. x0+7 of row y (0xff outside the image) -> known and hole bits
+    uint2 v = make_uint2(0xffffffffu, 0xffffffffu);
+    if (y >= 0 && y < H && x0 < W) {
+        const uint8_t *row = labels + (size_t)y * W;
+        if (vec8) {
+            v = __ldg(reinterpret_cast<const uint2 *>(row + x0));
+        } else {
+            uint32_t b[8];
+#pragma unroll
+            for (int c = 0; c < 8; c++) b[c] = (x0 + c < W) ? (uint32_t)__ldg(row + x0 + c) : 0xffu;
+            v.x = b[0] | (b[1] << 8) | (b[2] << 16) | (b[3] << 24);
+            v.y = b[4] | (b[5] << 8) | (b[6] << 16) | (b[7] << 24);
+        }
+    }
+    uint32_t k = 0, h = 0;
+#pragma unroll
+    for (int c = 0; c < 8; c++) {
+        const uint32_t l = ((c < 4 ? v.x : v.y) >> (8 * (c & 3))) & 0xffu;
+        k |= (uint32_t)(l == 0) << c;
+        h |= (uint32_t)(l == 1) << c;
+    }
+    kn = k;
+    ho = h;
+}
+
+__global__ void __launch_bounds__(32 * INIT_WARPS) init_kernel(const __grid_constant__ InitArgs a)
+{
+    const int b = blockIdx.x;
     int lo = 0, hi = a.n_frames;  // frame f with cta_offset[f] <= b < cta_offset[f+1]
     while (hi - lo > 1) {
         int mid = (lo + hi) >> 1;
         if (__ldg(&a.cta_offset[mid]) <= b) lo = mid; else hi = mid;
     }
     const FrameDev &F = a.frames[lo];
-    const int H = F.H, W = F.W;
-    const int strips = (W + 255) >> 8;
-    const int local = b - __ldg(&a.cta_offset[lo]);
-    const int band = local / strips;
-    const int x0 = (local - band * strips) * 256;
-    const int yb = band * TILE * INIT_STRIPS;
-    const int t = threadIdx.x;
-    // 16-byte label loads and state-word stores when every row starts on a 16-byte boundary
-    const bool vec = (W & 15) == 0 && (reinterpret_cast<uintptr_t>(F.labels) & 15u) == 0 &&
-                     (reinterpret_cast<uintptr_t>(F.shell) & 15u) == 0;
+    const int H = F.H, W = F.W, TW = F.TW, TH = F.TH;
+    const int strips = (TW + 31) >> 5;
+    const int unit = (b - __ldg(&a.cta_offset[lo])) * INIT_WARPS + (threadIdx.x >> 5);
+    if (unit >= TH * strips) return;  // warp-uniform
+    const int lane = threadIdx.x & 31;
+    const int ty = unit / strips, sx = unit - ty * strips;
+    const int tx = sx * 32 + lane;
+    const bool tile_ok = tx < TW;
+    const int x0 = tx * TILE, y0 = ty * TILE;
+    const bool vec8 = (W & 7) == 0 && (reinterpret_cast<uintptr_t>(F.labels) & 7u) == 0;
+    const bool vec16 = (W & 7) == 0 && (reinterpret_cast<uintptr_t>(F.shell) & 15u) == 0 &&
+                       (!F.enter || (reinterpret_cast<uintptr_t>(F.enter) & 15u) == 0);
 
-    if (vec) {
-        for (int e = t; e < LR * 18; e += 256) {
-            const int r = e / 18, c = e - r * 18;
-            const int y = yb - 1 + r, x = x0 - 16 + 16 * c;
-            uint4 v = make_uint4(0xffffffffu, 0xffffffffu, 0xffffffffu, 0xffffffffu);
-            if (y >= 0 && y < H && x >= 0 && x < W) v = __ldg(reinterpret_cast<const uint4 *>(F.labels + (size_t)y * W + x));
-            *reinterpret_cast<uint4 *>(&lab_s[r][16 * c]) = v;
-        }
-    } else {
-        for (int e = t; e < LR * 258; e += 256) {
-            const int r = e / 258, c = e - r * 258;
-            const int y = yb - 1 + r, x = x0 - 1 + c;
-            uint8_t v = 0xff;
-            if (y >= 0 && y < H && x >= 0 && x < W) v = __ldg(&F.labels[(size_t)y * W + x]);
-            lab_s[r][c + 15] = v;
-        }
+    // rows y0-1 .. y0+8: bit 0 = column x0-1, bits 1..8 = x0 .. x0+7, bit 9 = x0+8
+    uint32_t kn[TILE + 2], ho[TILE + 2];
+#pragma unroll
+    for (int r = 0; r < TILE + 2; r++) {
+        const int y = y0 - 1 + r;
+        uint32_t k8 = 0, h8 = 0;
+        if (tile_ok) init_label_row(F.labels, W, H, y, x0, vec8, k8, h8);
+        // the neighbouring columns: from the adjacent lanes, or from memory at the strip's ends
+        uint32_t kl = (__shfl_up_sync(FULL, k8, 1) >> 7) & 1u;
+        uint32_t kr = __shfl_down_sync(FULL, k8, 1) & 1u;
+        const bool rowin = y >= 0 && y < H;
+        if (lane == 0) kl = (rowin && x0 > 0 && x0 - 1 < W) ? (uint32_t)(__ldg(&F.labels[(size_t)y * W + x0 - 1]) == 0) : 0u;
+        if (lane == 31) kr = (rowin && x0 + 8 < W) ? (uint32_t)(__ldg(&F.labels[(size_t)y * W + x0 + 8]) == 0) : 0u;
+        kn[r] = kl | (k8 << 1) | (kr << 9);
+        ho[r] = h8 << 1;
     }
-    __syncthreads();
-
-    const int x = x0 + t;
-    const int lane = t & 31;
-    const bool data = (a.flags & GF_FLAG_DATA) != 0;
-    int gcount = 0;  // data term: hole pixels of this warp's columns with g != 0
-    for (int sub = 0; sub < INIT_STRIPS; sub++) {
-    const int ty = band * INIT_STRIPS + sub;  // tile row of the strip
-    const int y0 = ty * TILE;
-    if (y0 >= H) break;  // CTA-uniform
-    const int lr = TILE * sub;                // label row of the strip's row -1
-    unsigned long long Um[4] = {0, 0, 0, 0}, Qm[4] = {0, 0, 0, 0};
+    // tile masks and state words of rows y0 .. y0+7
+    unsigned long long U = 0ull, Q = 0ull;
 #pragma unroll
-    for (int r = 0; r < TILE; r++) {
-        int y = y0 + r;
-        bool in = (y < H) && (x < W);
-        uint8_t l = in ? lab_s[lr + r + 1][t + 16] : 0xff;
-        bool hole = in && l == 1;
-        bool front = false;
-        if (hole) {
+    for (int r = 1; r <= TILE; r++) {
+        uint32_t nb = kn[r - 1] | kn[r + 1];
+        nb |= (nb << 1) | (nb >> 1) | (kn[r] << 1) | (kn[r] >> 1);
+        const uint32_t f = ho[r] & nb;
+        const uint32_t urow = (ho[r] >> 1) & 0xffu, qrow = (f >> 1) & 0xffu;
+        U |= (unsigned long long)urow << (8 * (r - 1));
+        Q |= (unsigned long long)qrow << (8 * (r - 1));
+        const int y = y0 + r - 1;
+        if (!tile_ok || y >= H) continue;
+        // state word: -1 known, -2 hole, -3 anything else (bystander); outside the
+        // image nothing is written
+        const uint32_t known = (kn[r] >> 1) & 0xffu;
+        int32_t sw[8], en[8];
 #pragma unroll
-            for (int dy = 0; dy < 3; dy++)
-#pragma unroll
-                for (int dx = 0; dx < 3; dx++)
-                    if (!(dx == 1 && dy == 1) && lab_s[lr + r + dy][t + 15 + dx] == 0) front = true;
+        for (int c = 0; c < 8; c++) {
+            sw[c] = ((known >> c) & 1u) ? SH_KNOWN : (((urow >> c) & 1u) ? SH_UNFILLED : SH_BYST);
+            en[c] = ((qrow >> c) & 1u) ? 0 : -1;
         }
-        const int32_t sw = (l == 0) ? SH_KNOWN : (l == 1 ? SH_UNFILLED : SH_BYST);
-        if (vec) out_s[r][t] = sw;
-        else if (in) F.shell[(size_t)y * W + x] = sw;
-        if (in && F.enter) F.enter[(size_t)y * W + x] = front ? 0 : -1;  // optional map, plain stores
-        unsigned hb = __ballot_sync(FULL, hole);
-        unsigned fb = __ballot_sync(FULL, front);
-        if (data) {
-            bool gz = false;
-            if (hole) {
-                const float2 gv = __ldg(&F.guide[(size_t)y * W + x]);
-                gz = gv.x != 0.0f || gv.y != 0.0f;
+        const size_t o = (size_t)y * W + x0;
+        if (vec16) {
+            reinterpret_cast<int4 *>(F.shell + o)[0] = make_int4(sw[0], sw[1], sw[2], sw[3]);
+            reinterpret_cast<int4 *>(F.shell + o)[1] = make_int4(sw[4], sw[5], sw[6], sw[7]);
+            if (F.enter) {
+                reinterpret_cast<int4 *>(F.enter + o)[0] = make_int4(en[0], en[1], en[2], en[3]);
+                reinterpret_cast<int4 *>(F.enter + o)[1] = make_int4(en[4], en[5], en[6], en[7]);
             }
-            gcount += __popc(__ballot_sync(FULL, gz));
-        }
+        } else {
 #pragma unroll
-        for (int q = 0; q < 4; q++) {
-            Um[q] |= (unsigned long long)((hb >> (8 * q)) & 0xffu) << (8 * r);
-            Qm[q] |= (unsigned long long)((fb >> (8 * q)) & 0xffu) << (8 * r);
+            for (int c = 0; c < 8; c++) {
+                if (x0 + c < W) {
+                    F.shell[o + c] = sw[c];
+                    if (F.enter) F.enter[o + c] = en[c];
+                }
+            }
         }
     }
-    if (vec) {
-        __syncthreads();
-        for (int e = t; e < TILE * 64; e += 256) {
-            const int r = e >> 6, c4 = e & 63;
-            const int y = y0 + r, x = x0 + 4 * c4;
-            if (y < H && x < W)
-                *reinterpret_cast<int4 *>(F.shell + (size_t)y * W + x) = *reinterpret_cast<const int4 *>(&out_s[r][4 * c4]);
-        }
-        __syncthreads();  // out_s is rewritten by the next strip
-    }
-    const int warp = t >> 5;
-    bool has_front = false;
-    int tile = 0, nq = 0;
-    if (lane < 4) {
-        int tx = (x0 >> 3) + warp * 4 + lane;
-        if (tx < F.TW && y0 < H) {
-            tile = ty * F.TW + tx;
-            unsigned long long u = lane == 0 ? Um[0] : lane == 1 ? Um[1] : lane == 2 ? Um[2] : Um[3];
-            unsigned long long q = lane == 0 ? Qm[0] : lane == 1 ? Qm[1] : lane == 2 ? Qm[2] : Qm[3];
-            F.U[tile] = u;
-            F.Qw[tile] = q;
-            F.sched[tile] = -1;
-            F.F[tile].tag = INT32_MIN;
-            F.F[F.ntiles + tile].tag = INT32_MIN;
-            int c = __popcll(u);
-            if (c) atomicAdd(F.holes, c);
-            has_front = q != 0ull;
-            nq = __popcll(q);
+    int gcount = 0;  // data term: hole pixels of this tile with g != 0
+    if ((a.flags & GF_FLAG_DATA) && tile_ok) {
+        for (unsigned long long m = U; m; m &= m - 1ull) {
+            const int pix = __ffsll((long long)m) - 1;
+            const float2 gv = __ldg(&F.guide[(size_t)(y0 + (pix >> 3)) * W + x0 + (pix & 7)]);
+            gcount += (gv.x != 0.0f || gv.y != 0.0f) ? 1 : 0;
         }
     }
+    const int t = ty * TW + tx;
+    if (tile_ok) {
+        F.U[t] = U;
+        F.Qw[t] = Q;
+        F.sched[t] = -1;
+        F.F[t].tag = INT32_MIN;
+        F.F[F.ntiles + t].tag = INT32_MIN;
+    }
+    const int holes = __reduce_add_sync(FULL, __popcll(U));
+    const int nq = __reduce_add_sync(FULL, __popcll(Q));
+    gcount = __reduce_add_sync(FULL, gcount);
     // step-0 work list: warp-aggregated append of the tiles on the initial front
+    const bool has_front = Q != 0ull;
     const unsigned bm = __ballot_sync(FULL, has_front);
-    nq = __reduce_add_sync(FULL, nq);
-    if (bm) {
-        int b0 = 0;
-        if (lane == 0) {
+    int b0 = 0;
+    if (lane == 0) {
+        if (holes) atomicAdd(F.holes, holes);
+        if (gcount) atomicAdd(F.gleft, gcount);
+        if (bm) {
             b0 = atomicAdd(&F.init_count[0], __popc(bm));
             atomicAdd(&F.init_count[1], nq);
         }
-        b0 = __shfl_sync(FULL, b0, 0);
-        if (has_front) F.init_list[b0 + __popc(bm & ((1u << lane) - 1u))] = tile;
     }
-    }
-    if (data && lane == 0 && gcount) atomicAdd(F.gleft, gcount);
+    b0 = __shfl_sync(FULL, b0, 0);
+    if (has_front) F.init_list[b0 + __popc(bm & ((1u << lane) - 1u))] = t;
 }
 
 __global__ void upload_frames_kernel(const __grid_constant__ FrameChunk c)

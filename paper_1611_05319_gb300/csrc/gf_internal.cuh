@@ -17,9 +17,12 @@ constexpr int CTA_THREADS = WARPS_PER_CTA * 32;
 // whose state-window loads need more than the 128 registers a thread gets at
 // 16 warps.
 __host__ __device__ constexpr int fill_warps(int rw) { return rw == 8 ? 12 : 16; }
-// init kernel: CTAs of a frame (bands of INIT_STRIPS strips of 8 rows x 256 columns)
-constexpr int INIT_STRIPS = 4;
-__host__ __device__ inline int init_ctas(int TH, int W) { return ((TH + INIT_STRIPS - 1) / INIT_STRIPS) * ((W + 255) / 256); }
+// init kernel: CTAs of a frame (INIT_WARPS warps, one strip of 8 rows x 256 columns each)
+constexpr int INIT_WARPS = 8;
+__host__ __device__ inline int init_ctas(int TH, int W) {
+    const int strips = ((W + 7) / 8 + 31) / 32;
+    return (TH * strips + INIT_WARPS - 1) / INIT_WARPS;
+}
 
 // Per-pixel state word (out_shell): readable at step k  <=>  (uint)(s+1) < (uint)(k+1)
 constexpr int32_t SH_KNOWN = -1;
