@@ -56,6 +56,26 @@ def _gpu_fwd_bwd(img, lab, mag, phi, grad_out, mu, eps=3.0):
                 stats=r[0].stats(), gi=gi[0].cpu().numpy(), gphi=gp[0].cpu().numpy(), gmu=float(gmu[0]))
 
 
+# Per-pixel bound on the angle gradient: |g_gpu - g_oracle| <= ANG_RTOL * max(|g_oracle|, floor)
+# with floor = ANG_FLOOR * max |g_oracle| over the frame (below the floor the FP32
+# sums' absolute error, a few ulp of the largest terms times the number of steps,
+# dominates any relative bound).
+ANG_RTOL, ANG_FLOOR = 1e-3, 1e-2
+
+
+def assert_angle_grad(got, want):
+    """Element by element; reports the worst pixel."""
+    top = float(np.abs(want).max())
+    if top == 0.0:
+        assert np.abs(got).max() == 0.0
+        return 0.0
+    den = np.maximum(np.abs(want), ANG_FLOOR * top)
+    rel = np.abs(got - want) / den
+    i = np.unravel_index(int(np.argmax(rel)), rel.shape)
+    assert rel[i] <= ANG_RTOL, f"worst pixel {i}: gpu {got[i]} oracle {want[i]} (rel {rel[i]:.2e}, max {top:.3e})"
+    return float(rel[i])
+
+
 def test_guide_from_angle_bitexact():
     img, lab, mag, phi, guide, gt = _angle_problem(201)
     r = _gpu_fwd_bwd(img, lab, mag, phi, np.zeros_like(img), 10.0)
@@ -76,9 +96,7 @@ def test_adjoint_matches_oracle_reverse_sweep(seed, mu, band):
     gi, gphi, gmu = oracle.fill_backward(o["u"], lab, guide, o["shell"], o["stall_steps"], grad_out, eps=3.0, mu=mu)
     scale = np.abs(gi).max()
     assert np.abs(r["gi"] - gi).max() <= 1e-4 * max(1.0, scale)
-    nrm = np.linalg.norm(gphi)
-    if nrm > 0:
-        assert np.linalg.norm(r["gphi"] - gphi) <= 1e-3 * nrm
+    assert_angle_grad(r["gphi"], gphi)
     assert abs(r["gmu"] - gmu) <= 1e-3 * max(abs(gmu), 1e-6) + 1e-6
 
 
@@ -110,7 +128,8 @@ def test_fd_on_64x64_crop():
         fd.append((lp - lm) / (2 * h))
         got.append(r["gphi"][y, x])
     fd, got = np.array(fd), np.array(got)
-    assert np.linalg.norm(fd - got) <= 1e-3 * np.linalg.norm(fd) + 1e-7
+    # each sampled pixel on its own: relative 1e-3 above a floor of 1e-2 of the largest
+    assert_angle_grad(got, fd)
     fdm = (loss(mu=mu + 1e-5, phi=phi0) - loss(mu=mu - 1e-5, phi=phi0)) / 2e-5
     assert abs(fdm - r["gmu"]) <= 1e-3 * abs(fdm) + 1e-7, (fdm, r["gmu"])
 
@@ -134,7 +153,7 @@ def test_autograd_function_batch():
         gi, gphi, gmu = oracle.fill_backward(o["u"], p[1], p[4], o["shell"], o["stall_steps"], o["u"] - p[5],
                                              eps=3.0, mu=10.0)
         assert np.abs(img.grad[i].cpu().numpy() - gi).max() <= 1e-4 * max(1.0, np.abs(gi).max())
-        assert np.linalg.norm(phi.grad[i].cpu().numpy() - gphi) <= 1e-3 * max(np.linalg.norm(gphi), 1e-9)
+        assert_angle_grad(phi.grad[i].cpu().numpy(), gphi)
     assert mu.grad is not None and np.isfinite(float(mu.grad))
 
 
@@ -171,6 +190,15 @@ def test_differentiable_config_two_frames_of_sixteen():
         ogi, ogp, ogm = oracle.fill_backward(o["u"], p[1], guide, o["shell"], o["stall_steps"], go, eps=3.0,
                                              mu=50.0)
         assert np.abs(gi[i].cpu().numpy() - ogi).max() <= 1e-4 * max(1.0, np.abs(ogi).max())
-        if np.linalg.norm(ogp) > 0:
-            assert np.linalg.norm(gp[i].cpu().numpy() - ogp) <= 1e-3 * np.linalg.norm(ogp)
+        assert_angle_grad(gp[i].cpu().numpy(), ogp)
         assert abs(float(gmu[i]) - ogm) <= 1e-3 * abs(ogm) + 1e-6
+        if i == 0:
+            # FP64 central difference of the loss in mu on the whole 512 x 512 frame
+            # (frozen schedule, the adjoint's semantics), against the GPU's d/dmu
+            def loss(m):
+                u = oracle.frozen_fill(p[0], p[1], guide, o["shell"], o["stall_steps"], eps=3.0, mu=m)
+                return 0.5 * float(np.sum((u - p[0]) ** 2))
+            h = 1e-4
+            fdm = (loss(50.0 + h) - loss(50.0 - h)) / (2 * h)
+            assert fdm != 0.0
+            assert abs(float(gmu[i]) - fdm) <= 1e-3 * abs(fdm), (float(gmu[i]), fdm)
