@@ -16,8 +16,10 @@ e2e           the same step through the host-buffer C-ABI call (copies included)
 cpu_baseline  the FP64 CPU oracle on a bounded sample of the same frames
 
 --impl reference times the oracle (the reference arm of this workload) on the
-host cores.  Multi-GPU (torchrun): every rank fills its own copy of the batch
-(weak scaling, no data-path collective); the step time is the max over ranks.
+host cores.  Multi-GPU (torchrun): the job is 64 frames per GPU (seeds 100 ..
+100 + 64 N - 1) split over the ranks by longest-processing-time first on their
+hole fractions (weak scaling, no data-path collective); the step time is the max
+over ranks, the filled pixels the sum.
 """
 from __future__ import annotations
 
@@ -39,11 +41,10 @@ WORKLOAD = ("batched: 64 frames 1920x1080 RGBA fp32 (seeds 100-163), holes U[0.5
             "eps=3, mu=50, c=0.05, ghost ball, smart order, tracked front; in-place fill")
 SEED0, NFRAMES = 100, 64
 
-# DRAM traffic of fill_kernel per filled pixel from one ncu capture of the first 8
-# frames of this batch (dram__bytes_read.sum + dram__bytes_write.sum = 36.395008 MB +
-# 0.713216 MB for 534,164 filled pixels; profiles/fill_kernel_batch_8x1080.md).  It
-# holds only for the kernel sources it was taken on: with any other source the
-# roofline's traffic is reported as null.
+# DRAM traffic of fill_kernel per filled pixel from the ncu capture of the first 8
+# frames of this batch (dram__bytes_read.sum + dram__bytes_write.sum = 36.3904 MB +
+# 0.653568 MB for 534,164 filled pixels).  It holds only for the kernel sources it
+# was taken on: with any other source the roofline's traffic is reported as null.
 FILL_TRAFFIC = {
     "sources": {
         "paper_1611_05319_gb300/csrc/gf_fill.cu": "6388e7e478e05f0e2e432b3152802ea6bdd3fd45a8be07da001e8ac82f37a04e",
@@ -228,8 +229,16 @@ def main():
     build.build()
     ctx = gf.Context(local)
 
-    n = args.frames
-    frames = configs.batch_1080(n=n, seed0=SEED0)
+    # The job is `frames` frames per GPU: seeds SEED0 .. SEED0 + frames * world - 1,
+    # split over the ranks by longest-processing-time first on their hole fractions
+    # (weak scaling; one GPU fills exactly the 64-frame batch).
+    from paper_1611_05319_gb300.shard import lpt_partition
+    seeds = [SEED0 + i for i in range(args.frames * world)]
+    if world > 1:
+        mine = lpt_partition([int(1e6 * configs.batch_hole_fraction(sd)) for sd in seeds], world)[rank]
+        seeds = [seeds[i] for i in mine]
+    n = len(seeds)
+    frames = [configs.batch_frame(sd) for sd in seeds]
     H, W = frames[0]["labels"].shape
     rgba = torch.stack([torch.from_numpy(to_rgba(f["rgb"])) for f in frames]).to(dev)
     labels = torch.stack([torch.from_numpy(f["labels"]) for f in frames]).to(dev)
@@ -303,11 +312,12 @@ def main():
         launch += "; the %d largest holes on a second launch of %d clusters of %d" % (sm_, snc_, scs_)
     ms = t0.elapsed_time(t1) / K
     fill_ms = statistics.mean(a.elapsed_time(b) for a, b in ev_fill)
-    from paper_1611_05319_gb300.shard import max_over_ranks
+    from paper_1611_05319_gb300.shard import max_over_ranks, sum_over_ranks
     ms = max_over_ranks(ms, dist, dev)
     fill_ms = max_over_ranks(fill_ms, dist, dev)
     st = np.frombuffer(stats.cpu().numpy().tobytes(), dtype=_lib.STATS_DTYPE)
     filled = int(st["filled"].sum())
+    filled_job = sum_over_ranks(filled, dist, dev)
     bad = [int(s) for s in st["status"] if s < 0]
     chunks = (n + 127) // 128
     # guidance: descriptor upload(s), bin, guide; fill: descriptor upload(s), init, order, persistent fill
@@ -344,14 +354,14 @@ def main():
     roof = None
     try:
         gold = json.load(open(os.path.join(ROOT, "tests", "golden", "alg_bytes.json")))["frames"]["batch_1080"]
-        alg = sum(gold[str(SEED0 + i)]["alg_bytes"] for i in range(n))
+        alg = sum(gold[str(sd)]["alg_bytes"] for sd in seeds)
         peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
         peak, src = float(peaks["hbm_gbs"]), "measured"
     except Exception:
         alg, peak, src = None, 6800.0, "fallback"
     if alg is not None:
         ach = alg / (fill_ms / 1e3) / 1e9
-        filled_launch = sum(gold[str(SEED0 + i)]["filled"] for i in range(n))
+        filled_launch = sum(gold[str(sd)]["filled"] for sd in seeds)
         roof = {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
                 "traffic": fill_traffic(filled_launch), "kernel": "fill_kernel", "alg_bytes_per_launch": alg,
                 "fill_kernel_ms": fill_ms, "peak_source": src,
@@ -374,11 +384,26 @@ def main():
             se = ctx.fill_batched_host(hr, hl, None, hor, hos, splines=spl)
         w = (time.perf_counter() - w0) / args.e2e_steps
         w = max_over_ranks(w, dist, dev)
-        fe = int(se["filled"].sum())
+        fe = sum_over_ranks(int(se["filled"].sum()), dist, dev)
         h2d = sum(a.nbytes + b.nbytes for a, b in zip(hr, hl)) + sum(o.nbytes + p.nbytes for o, p in spl)
         d2h = sum(a.nbytes + b.nbytes for a, b in zip(hor, hos)) + n * _lib.STATS_BYTES
-        e2e = {"value": world * fe / w, "unit": "filled px/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+        e2e = {"value": fe / w, "unit": "filled px/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                "ms_per_step": w * 1e3, "call": "gf_fill_batched_host (pinned host buffers, splines in)"}
+
+    # ---- latency roofline: the longest shell chain of the batch at the measured
+    #      per-step floor of the fill kernel, against the fill kernel's time
+    latency = None
+    if rank == 0:
+        floor = leg_latency(ctx, dev, stream, 5)
+        k_max = int(st["shells"].max())
+        latency = {"k_max": k_max, "t_floor_us": floor["t_floor_us"],
+                   "chain_floor_ms": k_max * floor["t_floor_us"] / 1e3,
+                   "frac": k_max * floor["t_floor_us"] / 1e3 / fill_ms, "corridor": floor}
+        if roof is not None:
+            # the time per step of the longest chain at which the fill would run at
+            # half the HBM roofline
+            latency["us_per_step_for_half_hbm"] = roof["alg_bytes_per_launch"] / (0.5 * roof["peak"] * 1e3) / k_max
+            roof["latency"] = latency
 
     extra4k = adjoint = single = complexity = theorem1 = data_term = detect = None
     if rank == 0 and not args.no_extra:
@@ -394,16 +419,18 @@ def main():
         if dist:
             dist.destroy_process_group()
         return
-    value = world * filled / (ms / 1e3)
+    value = filled_job / (ms / 1e3)
     line = {
         "metric": METRIC, "value": value, "unit": "filled px/s", "n_gpus": world, "steps": K, "warmup": max(3, Wm),
         "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
         "data": "synthetic",
         "config": {"workload": WORKLOAD, "frames_per_gpu": n, "H": H, "W": W,
                    "filled_px_per_gpu_step": filled, "launch": launch,
+                   "sharding": "job of frames x N frames split over the N ranks by LPT on hole fraction; no "
+                               "collective in the data path",
                    "autotuned_cluster_size": tuned_cs, "autotune_fill_ms": tuned_ms,
                    "l2": "inputs 2.2 GB per GPU > 129 MB L2 (no flush); the init pass streams every frame each step"},
-        "frames_per_s": world * n / (ms / 1e3),
+        "frames_per_s": world * args.frames / (ms / 1e3),
         "plain": plain, "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
         "gpu_launches": launches_per_step * K, "clocks": clocks,
         "single_1080": single, "tracked_vs_rescan_4k": extra4k, "adjoint_16x512": adjoint,
@@ -480,6 +507,54 @@ def leg_1080(ctx, dev, stream, steps):
             "fill_kernel_ms": float(np.mean([a.elapsed_time(b) for a, b in evs])), "shells": int(st["shells"]),
             "filled_px": int(st["filled"]), "launch": "cluster %d x %d" % ctx.last_launch(),
             "workload": "1920x1080, bands of width U[3,15] px along 20 splines, ~3 % holes (seed 2), eps=3, mu=50"}
+
+
+def leg_latency(ctx, dev, stream, steps, L=4096):
+    """The per-step floor of the shell loop: a one-pixel corridor of L hole pixels
+    walled by bystanders and open at one end, onion order, so that every step
+    fills exactly one pixel (L steps).  fill-kernel time / L at cluster sizes
+    4, 8 and 16 (one cluster)."""
+    import ctypes as C
+
+    import numpy as np
+    import torch
+
+    from paper_1611_05319_gb300 import _lib
+    from synth import configs, to_rgba
+    f = configs.corridor(L)
+    H, W = f["labels"].shape
+    lab = torch.from_numpy(f["labels"]).to(dev)
+    img = torch.from_numpy(to_rgba(f["rgb"])).to(dev)
+    g = torch.from_numpy(f["guide"]).to(dev)
+    shell = torch.empty((H, W), dtype=torch.int32, device=dev)
+    stats = torch.zeros((_lib.STATS_BYTES,), dtype=torch.uint8, device=dev)
+    fr = (_lib.Frame * 1)(_lib.Frame(H, W, img.data_ptr(), lab.data_ptr(), g.data_ptr(), img.data_ptr(),
+                                     shell.data_ptr(), None, None))
+    prm = _lib.make_params(eps=3.0, mu=50.0, c=0.05, smart=False)
+    L_ = _lib.lib()
+    sp = C.c_void_p(stream.cuda_stream)
+    out = {}
+    for cs in (4, 8, 16):
+        ctx.set_launch_config(cs, 1)
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        for a, b in evs:
+            a.record(stream)
+            b.record(stream)
+        for k in range(steps + 1):
+            e = evs[k - 1] if k > 0 else None
+            _lib.check(L_.gf_fill_batched_ex(ctx._h, 1, fr, C.byref(prm), C.c_void_p(stats.data_ptr()), sp,
+                                             C.c_void_p(e[0].cuda_event) if e else None,
+                                             C.c_void_p(e[1].cuda_event) if e else None), "fill", ctx._h)
+        torch.cuda.synchronize()
+        st = np.frombuffer(stats.cpu().numpy().tobytes(), dtype=_lib.STATS_DTYPE)[0]
+        if int(st["shells"]) != L or int(st["filled"]) != L:
+            raise RuntimeError(f"corridor: {int(st['shells'])} steps, {int(st['filled'])} px (expected {L})")
+        ms = float(np.median([a.elapsed_time(b) for a, b in evs]))
+        out[f"cluster_{cs}"] = {"fill_kernel_ms": ms, "t_step_us": 1e3 * ms / L}
+    ctx.set_launch_config(0, 0)
+    out["t_floor_us"] = min(v["t_step_us"] for v in out.values())
+    out["workload"] = f"1 x {L} px corridor (3 x {L + 2} frame, bystander walls), onion order: {L} steps of 1 px"
+    return out
 
 
 def leg_4k(ctx, dev, stream, steps):

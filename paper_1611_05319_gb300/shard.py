@@ -3,8 +3,9 @@
 Frames never read one another, so a batch splits across GPUs with no exchange
 in the data path.  ``lpt_partition`` balances the ranks by hole size (longest
 processing time first: each frame, largest first, goes to the least-loaded
-rank).  ``max_over_ranks`` is the only collective: the step time of a job is
-the slowest rank's.
+rank).  ``max_over_ranks`` and ``sum_over_ranks`` are the only collectives
+(timing and counts, outside the data path): the step time of a job is the
+slowest rank's, its pixel count the sum over the ranks.
 """
 from __future__ import annotations
 
@@ -37,3 +38,14 @@ def max_over_ranks(value: float, dist=None, device=None) -> float:
     t = torch.tensor([float(value)], dtype=torch.float64, device=device)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t[0])
+
+
+def sum_over_ranks(value: int, dist=None, device=None) -> int:
+    """Sum of the integer ``value`` over the ranks of the default process group
+    (identity without one)."""
+    if dist is None or not dist.is_available() or not dist.is_initialized():
+        return int(value)
+    import torch
+    t = torch.tensor([int(value)], dtype=torch.int64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return int(t[0])

@@ -61,11 +61,16 @@ def frame_4k_blob(seed: int = 3, poison: bool = False, H: int = 2160, W: int = 3
                    eps=4.0, blob_xy=(bx, by))
 
 
+def batch_hole_fraction(seed: int) -> float:
+    """The target hole fraction of batch frame ``seed`` (U[0.5%, 8%]), without
+    building the frame."""
+    return float(_rng(seed + 4242).uniform(0.005, 0.08))
+
+
 def batch_frame(seed: int, poison: bool = False, H: int = 1080, W: int = 1920):
     """One frame of the uneven batch: hole fraction U[0.5%, 8%], band widths
     U[2, 40] px (half-widths U[1, 20])."""
-    rng = _rng(seed + 4242)
-    frac = float(rng.uniform(0.005, 0.08))
+    frac = batch_hole_fraction(seed)
     img = polygon_image(H, W, 40, seed)
     ctrl, hws, hole = bands_with_fraction(H, W, 20, seed, (1.0, 20.0), frac)
     return _finish(img, hole, poison=poison, splines=flatten_beziers(ctrl), half_widths=hws,
@@ -102,3 +107,20 @@ def line_problem(H: int, poison: bool = False):
     img[line] = np.array([0.9, 0.2, 0.1], np.float32)
     hole = ((yc >= 0.2) & (yc <= 0.8))[:, None] & ((xc >= 0.4) & (xc <= 3.96))[None, :]
     return _finish(img, hole, poison=poison, guide=np.zeros((H, W, 2), np.float32), smart=False)
+
+
+def corridor(L: int = 2048, poison: bool = False):
+    """A one-pixel-wide corridor of L hole pixels (row 1, x = 1..L) between two
+    rows of bystanders, open to one known pixel at its left end (0, 1) and closed
+    by a bystander at its right end: under onion order each step can fill only
+    the next pixel of the corridor, so the fill takes exactly L steps of one
+    pixel each (the per-step cost of the shell loop with no work in it).
+    Guide field 0, smart order off."""
+    H, W = 3, L + 2
+    img = np.full((H, W, 3), 0.5, np.float32)
+    img[1, 0] = (0.9, 0.2, 0.1)
+    hole = np.zeros((H, W), bool)
+    hole[1, 1:L + 1] = True
+    byst = np.ones((H, W), bool)
+    byst[1, 0:L + 1] = False
+    return _finish(img, hole, byst, poison=poison, guide=np.zeros((H, W, 2), np.float32), smart=False)

@@ -107,6 +107,28 @@ def test_stall_rule_band_across_image():
     assert_parity(o, r, lab)
 
 
+@pytest.mark.parametrize("cs", [4, 16])
+def test_corridor_one_pixel_per_step(cs):
+    """The benchmark's per-step floor workload: a one-pixel corridor walled by
+    bystanders fills one pixel per step under onion order."""
+    import torch
+
+    import paper_1611_05319_gb300 as gf
+    d = configs.corridor(300, poison=True)
+    ctx = gf.Context(0)
+    ctx.set_launch_config(cs, 1)
+    lab = d["labels"]
+    r = ctx.fill(torch.from_numpy(rgba(d["rgb"])).cuda(), torch.from_numpy(lab).cuda(),
+                 torch.from_numpy(d["guide"]).cuda(), smart=False, enter=True, stall=True)
+    torch.cuda.synchronize()
+    g = dict(u=r.rgba.cpu().numpy(), shell=r.shell.cpu().numpy(), enter=r.enter.cpu().numpy(), stats=r.stats(),
+             stall_steps=r.stall_steps())
+    o = oracle_fill(d["rgb"], lab, d["guide"], smart=False)
+    assert o["stats"]["shells"] == 300 and o["stats"]["max_front"] == 1
+    assert_parity(o, g, lab)
+    ctx.close()
+
+
 def test_walled_region_incomplete():
     H, W = 30, 30
     hole = synth.rect_mask(H, W, 5, 5, 8, 8) | synth.rect_mask(H, W, 20, 20, 3, 3)

@@ -83,3 +83,18 @@ def test_line_problem_geometry(H):
     line = (yc >= 0.45) & (yc <= 0.55)
     assert np.allclose(d["gt"][line], [0.9, 0.2, 0.1]) and np.allclose(d["gt"][~line], [0.1, 0.3, 0.8])
     assert not d["guide"].any() and d["smart"] is False
+
+
+def test_corridor_recipe():
+    """One-pixel corridor: L hole pixels in row 1, bystander walls, one known pixel at the open end."""
+    d = configs.corridor(50)
+    lab = d["labels"]
+    assert lab.shape == (3, 52)
+    assert (lab[1, 1:51] == 1).all() and lab[1, 0] == 0 and lab[1, 51] == 2
+    assert (lab[0] == 2).all() and (lab[2] == 2).all()
+    assert (d["guide"] == 0).all() and d["smart"] is False
+
+
+def test_batch_hole_fraction_is_the_frame_target():
+    for s in (100, 119, 163):
+        assert configs.batch_hole_fraction(s) == configs.batch_frame(s, H=108, W=192)["target_fraction"]
