@@ -30,8 +30,13 @@
 // treats as readable, so fills are written in place (Algorithm 1 evaluates
 // every front pixel against D^(k)).
 //
-// Mutable global data is read with ld.global.cg (L2) so that no SM reads a
-// stale L1 line written by another SM of the cluster.
+// Mutable global data is read with plain (weak) loads.  Every value a step reads
+// was written before the cluster barrier that began the step (whose wait has
+// acquire semantics at cluster scope, so the loads observe those writes), or is
+// being written during the step by another warp, in which case the old and the
+// new value lead to the same decision: a state word becoming k is unreadable at
+// step k like the -2 it replaces, and a neighbour's unfilled mask only filters
+// claims.
 
 #include <cooperative_groups.h>
 
@@ -42,6 +47,13 @@ namespace cg = cooperative_groups;
 namespace gf {
 
 constexpr unsigned FULL = 0xffffffffu;
+
+// A plain load (weak, may be served by L1); see the note on mutable data above.
+template <class T>
+__device__ __forceinline__ T ld(const T *p)
+{
+    return *p;
+}
 
 // The sample table of the fill kernel in shared memory: (n, m, 1/|(n, m)|, |m|)
 // in grouped order, padded to a multiple of 32 (one 16-byte load per sample; the
@@ -213,10 +225,10 @@ __global__ void upload_frames_kernel(const __grid_constant__ FrameChunk c)
 __global__ void order_kernel(const FrameDev *frames, int n, int32_t *order, int32_t *cursor)
 {
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-        int hi = __ldcg(frames[i].holes);
+        int hi = ld(frames[i].holes);
         int rank = 0;
         for (int j = 0; j < n; j++) {
-            int hj = __ldcg(frames[j].holes);
+            int hj = ld(frames[j].holes);
             if (hj > hi || (hj == hi && j < i)) rank++;
         }
         order[rank] = i;
@@ -458,8 +470,8 @@ __device__ void process_tile(const FillParams &p, const FrameDev &F, WarpSmem<RW
     // Issue every load that depends only on the tile before using any of them:
     // tile masks, the neighbours' step-(k-1) fills and hole masks, the state
     // window, the guide vectors and (speculatively) the colour window.
-    const unsigned long long U = __ldcg(&F.U[t]);
-    const unsigned long long Qold = __ldcg(&F.Qw[t]);
+    const unsigned long long U = ld(&F.U[t]);
+    const unsigned long long Qold = ld(&F.Qw[t]);
     int ftag = INT32_MIN;
     unsigned long long fmsk = 0ull, unb = 0ull;
     const int ndx = lane % 3 - 1, ndy = lane / 3 - 1;
@@ -467,11 +479,11 @@ __device__ void process_tile(const FillParams &p, const FrameDev &F, WarpSmem<RW
     const bool nvalid = lane < 9 && nxt_x >= 0 && nxt_y >= 0 && nxt_x < F.TW && nxt_y < F.TH;
     const int nt = nxt_y * F.TW + nxt_x;
     if (MODE != RESCAN && nvalid) {
-        unb = __ldcg(&F.U[nt]);
+        unb = ld(&F.U[nt]);
         if (MODE == NORMAL && k > 0) {
             const TileF *e = &F.F[(size_t)((k - 1) & 1) * F.ntiles + nt];
-            ftag = __ldcg(&e->tag);
-            fmsk = __ldcg(&e->mask);
+            ftag = ld(&e->tag);
+            fmsk = ld(&e->mask);
         }
     }
     const int wx0 = x0 - RW, wy0 = y0 - RW;
@@ -479,7 +491,7 @@ __device__ void process_tile(const FillParams &p, const FrameDev &F, WarpSmem<RW
 #pragma unroll
     for (int r = 0; r < WS; r++) {
         int gx = wx0 + lane, gy = wy0 + r;
-        sv[r] = (lane < WS && gx >= 0 && gy >= 0 && gx < W && gy < H) ? __ldcg(&F.shell[(size_t)gy * W + gx])
+        sv[r] = (lane < WS && gx >= 0 && gy >= 0 && gx < W && gy < H) ? ld(&F.shell[(size_t)gy * W + gx])
                                                                        : SH_OUTSIDE;
     }
     float2 gv[2] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
@@ -903,7 +915,7 @@ __device__ void sweep_tiles(const FillParams &p, const FrameDev &F, WarpSmem<RW>
     for (int base = gw * 32; base < F.ntiles; base += nw * 32) {
         int t = base + lane;
         unsigned long long m = 0;
-        if (t < F.ntiles) m = (MODE == RESCAN || MODE == REVAL) ? __ldcg(&F.U[t]) : __ldcg(&F.Qw[t]);
+        if (t < F.ntiles) m = (MODE == RESCAN || MODE == REVAL) ? ld(&F.U[t]) : ld(&F.Qw[t]);
         unsigned bal = __ballot_sync(FULL, m != 0ull);
         while (bal) {
             int i = __ffs(bal) - 1;
@@ -951,28 +963,28 @@ __global__ void __launch_bounds__(fill_warps(RW) * 32, 1) fill_kernel(const __gr
             ctl->rechecks = 0;
         }
         cluster.sync();
-        const int f = __ldcg(&ctl->cur_frame[it & 1]);
+        const int f = ld(&ctl->cur_frame[it & 1]);
         if (f >= p.n_frames) break;
         if (threadIdx.x == 0) s_frame = p.frames[p.frame_order[p.order_first + f]];
         __syncthreads();
         const FrameDev &F = s_frame;
 
-        long long n_front = __ldcg(&F.init_count[1]);
+        long long n_front = ld(&F.init_count[1]);
         long long filled_tot = 0, evals_tot = 0, max_front = 0;
         int stalls = 0, status = GF_OK;
         int k = 0;
         const int max_shells = F.max_shells;
         // the length and the first item of the current step's work list are loaded
         // ahead, together with the previous step's counters
-        int n_cur = __ldcg(&F.init_count[0]);
-        int t0_cur = gw < n_cur ? __ldcg(&F.init_list[gw]) : -1;
+        int n_cur = ld(&F.init_count[0]);
+        int t0_cur = gw < n_cur ? ld(&F.init_list[gw]) : -1;
         // eq. ready2 (GF_FLAG_DATA): phase 1 while hole pixels with g != 0 remain and
         // some front pixel is ready under the data term; `reval`: this step tests every
         // front pixel with eq. ready (the tracked front was built under phase 1)
         bool phase1 = (p.flags & GF_FLAG_DATA) != 0;
         int data_switch = -1;
         bool reval = false;
-        if (phase1 && __ldcg(F.gleft) == 0) {
+        if (phase1 && ld(F.gleft) == 0) {
             phase1 = false;
             data_switch = 0;
         }
@@ -1003,7 +1015,7 @@ __global__ void __launch_bounds__(fill_warps(RW) * 32, 1) fill_kernel(const __gr
                 if (more) {
                     int nxt = nw + __shfl_sync(FULL, pre, 0);
                     while (nxt < n) {
-                        const int t = __ldcg(&L[nxt]);
+                        const int t = ld(&L[nxt]);
                         if (lane0) pre = atomicAdd(&ctl->cursor[slot], 1);
                         if (t >= 0) process_tile<RW, NORMAL>(p, F, ws, ctl, lists, t, k, 0ull, wc, pc, more, phase1);
                         nxt = nw + __shfl_sync(FULL, pre, 0);
@@ -1016,13 +1028,13 @@ __global__ void __launch_bounds__(fill_warps(RW) * 32, 1) fill_kernel(const __gr
             // one round trip: this step's counters and the next step's list
             const int s3n = (k + 1) % 3;
             const int32_t *Ln = lists + (size_t)s3n * p.list_cap;
-            int filled = __ldcg(&ctl->filled[slot]);
-            int dlt = __ldcg(&ctl->front_delta[slot]);
-            const int ev = __ldcg(&ctl->evals[slot]);
-            const int er = __ldcg(&ctl->err[slot]);
-            int n_next = __ldcg(&ctl->list_count[s3n]);
-            int t0_next = gw < p.list_cap ? __ldcg(&Ln[gw]) : -1;  // used only if gw < n_next
-            const int gleft = phase1 ? __ldcg(F.gleft) : -1;
+            int filled = ld(&ctl->filled[slot]);
+            int dlt = ld(&ctl->front_delta[slot]);
+            const int ev = ld(&ctl->evals[slot]);
+            const int er = ld(&ctl->err[slot]);
+            int n_next = ld(&ctl->list_count[s3n]);
+            int t0_next = gw < p.list_cap ? ld(&Ln[gw]) : -1;  // used only if gw < n_next
+            const int gleft = phase1 ? ld(F.gleft) : -1;
             evals_tot += ev;
             if (er) {
                 status = GF_ERR_INTERNAL;
@@ -1041,11 +1053,11 @@ __global__ void __launch_bounds__(fill_warps(RW) * 32, 1) fill_kernel(const __gr
                 claims_drain(p, ctl, lists, pc, wr);
                 flush_counters(ctl, wr, k, true, false);
                 cluster.sync();
-                filled = __ldcg(&ctl->filled[slot]);
-                dlt = __ldcg(&ctl->front_delta[slot]);
-                const int er1 = __ldcg(&ctl->err[slot]);
-                n_next = __ldcg(&ctl->list_count[s3n]);
-                t0_next = gw < p.list_cap ? __ldcg(&Ln[gw]) : -1;
+                filled = ld(&ctl->filled[slot]);
+                dlt = ld(&ctl->front_delta[slot]);
+                const int er1 = ld(&ctl->err[slot]);
+                n_next = ld(&ctl->list_count[s3n]);
+                t0_next = gw < p.list_cap ? ld(&Ln[gw]) : -1;
                 if (er1) {
                     status = GF_ERR_INTERNAL;
                     break;
@@ -1069,12 +1081,12 @@ __global__ void __launch_bounds__(fill_warps(RW) * 32, 1) fill_kernel(const __gr
                 claims_drain(p, ctl, lists, pc, ws2);
                 flush_counters(ctl, ws2, k, true, false);
                 cluster.sync();
-                const int sf = __ldcg(&ctl->filled[slot]);
-                const int dlt2 = __ldcg(&ctl->front_delta[slot]);
-                const int er2 = __ldcg(&ctl->err[slot]);
+                const int sf = ld(&ctl->filled[slot]);
+                const int dlt2 = ld(&ctl->front_delta[slot]);
+                const int er2 = ld(&ctl->err[slot]);
                 // the stall fills appended claims to the next step's list
-                n_next = __ldcg(&ctl->list_count[s3n]);
-                t0_next = gw < p.list_cap ? __ldcg(&Ln[gw]) : -1;
+                n_next = ld(&ctl->list_count[s3n]);
+                t0_next = gw < p.list_cap ? ld(&Ln[gw]) : -1;
                 if (er2) {
                     status = GF_ERR_INTERNAL;
                     break;
@@ -1097,7 +1109,7 @@ __global__ void __launch_bounds__(fill_warps(RW) * 32, 1) fill_kernel(const __gr
             }
         }
         if (leader) {
-            const int holes = __ldcg(F.holes);
+            const int holes = ld(F.holes);
             gf_stats st;
             st.shells = k;
             st.stalls = stalls;
@@ -1105,7 +1117,7 @@ __global__ void __launch_bounds__(fill_warps(RW) * 32, 1) fill_kernel(const __gr
             st.evaluations = evals_tot;
             st.max_front = max_front;
             st.holes = holes;
-            st.rechecks = __ldcg(&ctl->rechecks);
+            st.rechecks = ld(&ctl->rechecks);
             st.data_switch = data_switch;
             st.reserved = 0;
             if (status == GF_OK && filled_tot < holes) status = GF_INCOMPLETE;
