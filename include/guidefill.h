@@ -188,6 +188,13 @@ gf_status gf_fill_batched_ex(gf_ctx *ctx, int n, const gf_frame *frames, const g
  * (gf_guidance_from_splines with `eta`); fills; and copies the filled image
  * and shell map back into host_out_rgba[i] / host_out_shell[i].  host_stats:
  * n gf_stats written on the host.  Synchronises `stream` before returning.
+ * In place (host_out_rgba[i] == host_rgba[i] for every frame) on host memory
+ * the device can address (pinned or registered; also host_guide[i] where
+ * given), only what the fill reads and writes crosses the link: the colours of
+ * the 8x8 tiles within one tile of a tile holding a hole pixel (the fill reads
+ * colours at most ceil(eps) + 1 <= 8 px from a hole pixel), the guide of the
+ * hole tiles, and back the colours of the hole pixels, written by the device
+ * into the caller's buffer; the buffer ends up as a full copy would leave it.
  */
 gf_status gf_fill_batched_host(gf_ctx *ctx, int n, const int32_t *H, const int32_t *W,
                                const float *const *host_rgba, const uint8_t *const *host_labels,

@@ -17,7 +17,8 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libguidefill.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["gf_fill.cu", "gf_guidance.cu", "gf_adjoint.cu", "gf_api.cu", "gf_noalloc.cu", "gf_detect.cu"]
+SOURCES = ["gf_fill.cu", "gf_guidance.cu", "gf_adjoint.cu", "gf_api.cu", "gf_noalloc.cu", "gf_detect.cu",
+           "gf_hostio.cu"]
 
 
 def _nvcc() -> str:

@@ -415,10 +415,14 @@ int gf_max_active_clusters(gf_ctx *ctx, float eps, int cluster_size)
     return n;
 }
 
+// host_rgba / host_shell (optional, n entries each): device-accessible host
+// buffers of an in-place host-buffer fill, read and written by the fill kernel
+// itself (FrameDev::host_rgba).
 static gf_status enqueue_fill(gf_ctx *ctx, int n, const gf_frame *frames, const gf_params *prm,
                               gf_stats *dev_stats, cudaStream_t stream, cudaEvent_t ev0 = nullptr,
                               cudaEvent_t ev1 = nullptr, bool allow_graph = true, DevBuf *scratch = nullptr,
-                              cudaEvent_t wait_before_fill = nullptr)
+                              cudaEvent_t wait_before_fill = nullptr, float4 *const *host_rgba = nullptr,
+                              int32_t *const *host_shell = nullptr)
 {
     DevBuf &arena = scratch ? *scratch : ctx->arena;
     // ---- layout of the scratch arena
@@ -528,6 +532,8 @@ static gf_status enqueue_fill(gf_ctx *ctx, int n, const gf_frame *frames, const 
         d.gleft = (int32_t *)(A + off_gleft) + i;
         d.init_list = (int32_t *)(A + off_L[i]);
         d.init_count = (int32_t *)(A + off_icnt) + 2 * i;
+        if (host_rgba) d.host_rgba = host_rgba[i];
+        if (host_shell) d.host_shell = host_shell[i];
         hd[i] = d;
         hcta[i] = (int32_t)ctas;
         ctas += (int64_t)init_ctas(d.TH, f.W);
@@ -1354,6 +1360,178 @@ gf_status gf_fill_backward(gf_ctx *ctx, int n, const gf_adjoint_frame *frames, c
     return GF_OK;
 }
 
+}  // extern "C"
+
+// The in-place host-buffer fill on device-accessible host memory: labels and
+// polylines in, the guide fields (from the polylines, or gathered from the
+// caller's guide fields at the hole tiles), then the batched fill in the
+// context's launch shape (autotuned or set), whose kernel reads the colours near
+// the holes from the caller's buffers and writes the hole pixels' colours and the
+// shell maps back (fill kernel: host_gather, host_write_back).
+static gf_status fill_host_in_place(gf_ctx *ctx, int n, const int32_t *H, const int32_t *W,
+                                    const uint8_t *const *host_labels, const int32_t *const *host_offsets,
+                                    const float *const *host_pts, const int32_t *n_splines, const int32_t *n_points,
+                                    float eta, int32_t *const *host_out_shell, const gf_params *params,
+                                    gf_stats *host_stats, cudaStream_t st, char *A, const std::vector<size_t> &o_rgba,
+                                    const std::vector<size_t> &o_lab, const std::vector<size_t> &o_g,
+                                    const std::vector<size_t> &o_sh, const std::vector<size_t> &o_off,
+                                    const std::vector<size_t> &o_pts, const std::vector<size_t> &o_th, size_t o_st,
+                                    const std::vector<char> &from_splines, const std::vector<float4 *> &dev_host_rgba,
+                                    const std::vector<const float2 *> &dev_host_guide)
+{
+    std::vector<gf_frame> fr(n);
+    std::vector<gf_spline_frame> sf;
+    std::vector<int32_t *> dev_host_shell(n, nullptr);
+    bool any_guide = false;
+    for (int i = 0; i < n; i++) {
+        const size_t np = (size_t)H[i] * W[i];
+        CK(cudaMemcpyAsync(A + o_lab[i], host_labels[i], np, cudaMemcpyHostToDevice, st));
+        if (from_splines[i] && n_splines[i] > 0) {
+            CK(cudaMemcpyAsync(A + o_off[i], host_offsets[i], 4 * (size_t)(n_splines[i] + 1), cudaMemcpyHostToDevice,
+                               st));
+            CK(cudaMemcpyAsync(A + o_pts[i], host_pts[i], 8 * (size_t)n_points[i], cudaMemcpyHostToDevice, st));
+        }
+        gf_frame &f = fr[i];
+        f.H = H[i];
+        f.W = W[i];
+        f.rgba = (const float *)(A + o_rgba[i]);
+        f.labels = (const uint8_t *)(A + o_lab[i]);
+        f.guide = (const float *)(A + o_g[i]);
+        f.out_rgba = (float *)(A + o_rgba[i]);
+        f.out_shell = (int32_t *)(A + o_sh[i]);
+        f.out_enter = nullptr;
+        f.out_stall = nullptr;
+        if (from_splines[i]) {
+            gf_spline_frame g;
+            g.H = H[i];
+            g.W = W[i];
+            g.labels = f.labels;
+            g.n_splines = n_splines[i];
+            g.n_points = n_points[i];
+            g.offsets = (const int32_t *)(A + o_off[i]);
+            g.pts = (const float *)(A + o_pts[i]);
+            g.guide = (float *)(A + o_g[i]);
+            g.weight = nullptr;
+            sf.push_back(g);
+        } else {
+            any_guide = true;
+        }
+        // the shell map goes straight into the caller's buffer when the device can
+        // address it, else through a copy after the fill
+        cudaPointerAttributes pa;
+        if (cudaPointerGetAttributes(&pa, host_out_shell[i]) == cudaSuccess && pa.type == cudaMemoryTypeHost &&
+            pa.devicePointer)
+            dev_host_shell[i] = (int32_t *)pa.devicePointer;
+        else
+            cudaGetLastError();
+    }
+    if (any_guide) {
+        // caller-given guide fields: those of the hole tiles, gathered by the device
+        for (int b = 0; b < n; b += HOSTIO_MAX) {
+            HostIOArgs ha;
+            memset(&ha, 0, sizeof(ha));
+            int max_tiles = 1, max_strips = 1;
+            for (int i = b; i < std::min(n, b + HOSTIO_MAX); i++) {
+                if (from_splines[i]) continue;
+                HostIOFrame &hf = ha.f[ha.n++];
+                hf.H = H[i];
+                hf.W = W[i];
+                hf.TW = (W[i] + 7) / 8;
+                hf.TH = (H[i] + 7) / 8;
+                hf.labels = (const uint8_t *)(A + o_lab[i]);
+                hf.host_guide = dev_host_guide[i];
+                hf.dev_guide = (float2 *)(A + o_g[i]);
+                hf.tile_hole = (uint8_t *)(A + o_th[i]);
+                max_tiles = std::max(max_tiles, hf.TW * hf.TH);
+                max_strips = std::max(max_strips, hf.TH * ((hf.TW + 31) / 32));
+            }
+            if (!ha.n) continue;
+            hostio_holes_kernel<<<dim3((unsigned)((max_tiles + 255) / 256), (unsigned)ha.n), 256, 0, st>>>(ha);
+            hostio_gather_kernel<<<dim3((unsigned)((max_strips + 7) / 8), (unsigned)ha.n), 256, 0, st>>>(ha);
+            CK(cudaGetLastError());
+        }
+    }
+    // Every colour moves inside the fill kernel.  The shell maps: where the device
+    // can address every one of them, each map is copied to the host on the copy
+    // stream as soon as the init pass has written it (every entry but the hole
+    // pixels' is then final), beside the fill, and after both a small kernel
+    // writes the hole pixels' final values; otherwise they are copied after the fill.
+    bool all_shell = true;
+    for (int i = 0; i < n; i++) all_shell = all_shell && dev_host_shell[i];
+    std::vector<float4 *> hr(dev_host_rgba.begin(), dev_host_rgba.end());
+    gf_stats *dst = (gf_stats *)(A + o_st);
+    while ((int)ctx->pipe_ev.size() < 2) {
+        cudaEvent_t ev;
+        CK(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+        ctx->pipe_ev.push_back(ev);
+    }
+    cudaEvent_t ev_init = all_shell ? ctx->pipe_ev[0] : nullptr;
+    gf_status s = GF_OK;
+    if (!sf.empty() && !(params->flags & GF_FLAG_DATA)) {
+        // guide fields on the context's second stream beside the fill's preparation
+        CK(cudaEventRecord(ctx->fork_ev, st));
+        CK(cudaStreamWaitEvent(ctx->aux, ctx->fork_ev, 0));
+        s = guidance_impl(ctx, ctx->garena, (int)sf.size(), sf.data(), eta, ctx->aux);
+        if (s != GF_OK) {
+            cudaStreamSynchronize(ctx->aux);
+            return s;
+        }
+        CK(cudaEventRecord(ctx->guide_ev, ctx->aux));
+        s = enqueue_fill(ctx, n, fr.data(), params, dst, st, ev_init, nullptr, true, nullptr, ctx->guide_ev,
+                         hr.data(), nullptr);
+        if (s != GF_OK) {
+            CK(cudaStreamWaitEvent(st, ctx->guide_ev, 0));
+            cudaStreamSynchronize(st);
+            return s;
+        }
+    } else {
+        if (!sf.empty()) {
+            s = guidance_impl(ctx, ctx->garena, (int)sf.size(), sf.data(), eta, st);
+            if (s != GF_OK) return s;
+        }
+        s = enqueue_fill(ctx, n, fr.data(), params, dst, st, ev_init, nullptr, true, nullptr, nullptr, hr.data(),
+                         nullptr);
+        if (s != GF_OK) {
+            cudaStreamSynchronize(st);
+            return s;
+        }
+    }
+    if (all_shell) {
+        CK(cudaStreamWaitEvent(ctx->copy_out, ev_init, 0));
+        for (int i = 0; i < n; i++)
+            CK(cudaMemcpyAsync(host_out_shell[i], A + o_sh[i], 4 * (size_t)H[i] * W[i], cudaMemcpyDeviceToHost,
+                               ctx->copy_out));
+        CK(cudaEventRecord(ctx->pipe_ev[1], ctx->copy_out));
+        CK(cudaStreamWaitEvent(st, ctx->pipe_ev[1], 0));
+        for (int b = 0; b < n; b += HOSTIO_MAX) {
+            HostIOArgs ha;
+            memset(&ha, 0, sizeof(ha));
+            int max_strips = 1;
+            for (int i = b; i < std::min(n, b + HOSTIO_MAX); i++) {
+                HostIOFrame &hf = ha.f[ha.n++];
+                hf.H = H[i];
+                hf.W = W[i];
+                hf.TW = (W[i] + 7) / 8;
+                hf.TH = (H[i] + 7) / 8;
+                hf.labels = (const uint8_t *)(A + o_lab[i]);
+                hf.dev_shell = (const int32_t *)(A + o_sh[i]);
+                hf.host_shell = dev_host_shell[i];
+                max_strips = std::max(max_strips, hf.TH * ((hf.TW + 31) / 32));
+            }
+            hostio_shell_fixup_kernel<<<dim3((unsigned)((max_strips + 7) / 8), (unsigned)ha.n), 256, 0, st>>>(ha);
+            CK(cudaGetLastError());
+        }
+    } else {
+        for (int i = 0; i < n; i++)
+            CK(cudaMemcpyAsync(host_out_shell[i], A + o_sh[i], 4 * (size_t)H[i] * W[i], cudaMemcpyDeviceToHost, st));
+    }
+    CK(cudaMemcpyAsync(host_stats, dst, sizeof(gf_stats) * (size_t)n, cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    return GF_OK;
+}
+
+extern "C" {
+
 gf_status gf_fill_batched_host(gf_ctx *ctx, int n, const int32_t *H, const int32_t *W,
                                const float *const *host_rgba, const uint8_t *const *host_labels,
                                const float *const *host_guide, const int32_t *n_splines,
@@ -1367,8 +1545,14 @@ gf_status gf_fill_batched_host(gf_ctx *ctx, int n, const int32_t *H, const int32
         return GF_ERR_ARG;
     gf_status s = check_params(params);
     if (s != GF_OK) return s;
-    std::vector<size_t> o_rgba(n), o_lab(n), o_g(n), o_sh(n), o_off(n), o_pts(n);
+    std::vector<size_t> o_rgba(n), o_lab(n), o_g(n), o_sh(n), o_off(n), o_pts(n), o_th(n);
     std::vector<char> from_splines(n, 0);
+    // In place (out_rgba == rgba) on host memory the device can address: only the
+    // colours near the holes come in and only the hole pixels' colours go out
+    // (fill_host_in_place); otherwise whole frames are copied both ways.
+    bool sparse = true;
+    std::vector<float4 *> dev_host_rgba(n, nullptr);
+    std::vector<const float2 *> dev_host_guide(n, nullptr);
     size_t pos = 0;
     for (int i = 0; i < n; i++) {
         if (H[i] <= 0 || W[i] <= 0 || !host_rgba[i] || !host_labels[i] || !host_out_rgba[i] || !host_out_shell[i])
@@ -1388,6 +1572,30 @@ gf_status gf_fill_batched_host(gf_ctx *ctx, int n, const int32_t *H, const int32
         o_sh[i] = pos; pos = align_up(pos + 4 * np, 256);
         o_off[i] = pos; pos = align_up(pos + (from_splines[i] ? 4 * (size_t)(n_splines[i] + 1) : 0), 256);
         o_pts[i] = pos; pos = align_up(pos + (from_splines[i] ? 8 * (size_t)n_points[i] : 0), 256);
+        o_th[i] = pos; pos = align_up(pos + (size_t)((W[i] + 7) / 8) * ((H[i] + 7) / 8), 256);
+    }
+    for (int i = 0; i < n && sparse; i++) {
+        if (host_out_rgba[i] != host_rgba[i]) {
+            sparse = false;
+            break;
+        }
+        cudaPointerAttributes pa;
+        if (cudaPointerGetAttributes(&pa, host_rgba[i]) != cudaSuccess || pa.type != cudaMemoryTypeHost ||
+            !pa.devicePointer) {
+            cudaGetLastError();
+            sparse = false;
+            break;
+        }
+        dev_host_rgba[i] = (float4 *)pa.devicePointer;
+        if (!from_splines[i]) {
+            if (cudaPointerGetAttributes(&pa, host_guide[i]) != cudaSuccess || pa.type != cudaMemoryTypeHost ||
+                !pa.devicePointer) {
+                cudaGetLastError();
+                sparse = false;
+                break;
+            }
+            dev_host_guide[i] = (const float2 *)pa.devicePointer;
+        }
     }
     const size_t o_st = pos; pos = align_up(pos + sizeof(gf_stats) * (size_t)n, 256);
     cudaError_t e = cudaSetDevice(ctx->device);
@@ -1396,6 +1604,9 @@ gf_status gf_fill_batched_host(gf_ctx *ctx, int n, const int32_t *H, const int32
     if (s != GF_OK) return s;
     char *A = (char *)ctx->io.ptr;
     cudaStream_t st = (cudaStream_t)stream;
+    if (sparse) return fill_host_in_place(ctx, n, H, W, host_labels, host_offsets, host_pts, n_splines, n_points,
+                                          eta, host_out_shell, params, host_stats, st, A, o_rgba, o_lab, o_g, o_sh,
+                                          o_off, o_pts, o_th, o_st, from_splines, dev_host_rgba, dev_host_guide);
     // Chunk pipeline: the frames' inputs are copied in on one stream; each chunk's
     // guide field, fill and output copies run on a stream of their own (with
     // scratch of their own) as soon as its inputs have landed, so chunks whose

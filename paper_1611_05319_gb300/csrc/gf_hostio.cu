@@ -1,0 +1,111 @@
+// Host-side inputs of the in-place host-buffer fill (gf_fill_batched_host with
+// out_rgba == rgba on device-accessible host memory) that the fill kernel does
+// not read itself: a caller-given guide field is needed at hole pixels only, so
+// only the guide of the 8x8 tiles holding a hole pixel is read from the caller's
+// buffer (the fill kernel gathers the colours it needs, near the holes, and
+// writes the hole pixels' colours and the shell map back).
+//
+// Kernels (one frame per blockIdx.y, up to HOSTIO_MAX frames per launch):
+//   hostio_holes_kernel    per 8x8 tile: does it hold a hole pixel (labels)
+//   hostio_gather_kernel   host -> device guide of the hole tiles (and colours of
+//                          the tiles next to a hole tile, where host_rgba is set)
+// The gather runs one warp per strip of 8 rows x 256 columns, lane l on the
+// columns l, l + 32, ... so that every access of a warp covers contiguous bytes
+// of a row.
+
+#include "gf_internal.cuh"
+
+namespace gf {
+
+namespace {
+constexpr unsigned FULLM = 0xffffffffu;
+}
+
+__global__ void __launch_bounds__(256) hostio_holes_kernel(const __grid_constant__ HostIOArgs a)
+{
+    if ((int)blockIdx.y >= a.n) return;
+    const HostIOFrame &F = a.f[blockIdx.y];
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= F.TW * F.TH) return;
+    const int tx = t % F.TW, ty = t / F.TW;
+    const int x0 = tx * TILE, y0 = ty * TILE;
+    bool any = false;
+    for (int r = 0; r < TILE && y0 + r < F.H; r++) {
+        const uint8_t *row = F.labels + (size_t)(y0 + r) * F.W;
+        for (int c = 0; c < TILE && x0 + c < F.W; c++) any |= row[x0 + c] == 1;
+    }
+    F.tile_hole[t] = any ? 1 : 0;
+}
+
+// The strip of warp `unit`: tile row ty, columns of tiles 32 s .. 32 s + 31.
+// Returns false (for the whole warp) past the frame's last strip.
+__device__ __forceinline__ bool hostio_strip(const HostIOFrame &F, int &ty, int &s)
+{
+    const int strips = (F.TW + 31) >> 5;
+    const int unit = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (unit >= F.TH * strips) return false;
+    ty = unit / strips;
+    s = unit - ty * strips;
+    return true;
+}
+
+__global__ void __launch_bounds__(256) hostio_gather_kernel(const __grid_constant__ HostIOArgs a)
+{
+    if ((int)blockIdx.y >= a.n) return;
+    const HostIOFrame &F = a.f[blockIdx.y];
+    int ty, s;
+    if (!hostio_strip(F, ty, s)) return;  // warp-uniform
+    const int lane = threadIdx.x & 31;
+    const int tx = s * 32 + lane;
+    // lane l: is tile 32 s + l next to (or holding) a hole pixel; does it hold one
+    bool rel = false, own = false;
+    if (tx < F.TW) {
+        own = F.tile_hole[ty * F.TW + tx] != 0;
+        for (int dy = -1; dy <= 1; dy++)
+            for (int dx = -1; dx <= 1; dx++) {
+                const int nx = tx + dx, ny = ty + dy;
+                if (nx >= 0 && ny >= 0 && nx < F.TW && ny < F.TH && F.tile_hole[ny * F.TW + nx]) rel = true;
+            }
+    }
+    const unsigned relm = __ballot_sync(FULLM, rel), ownm = __ballot_sync(FULLM, own);
+    if (!relm) return;
+    const int xs = s * 32 * TILE;
+    for (int r = 0; r < TILE; r++) {
+        const int y = ty * TILE + r;
+        if (y >= F.H) break;
+        const size_t row = (size_t)y * F.W;
+#pragma unroll
+        for (int i = 0; i < 8; i++) {
+            const int p = lane + 32 * i, x = xs + p;
+            const int j = p >> 3;  // tile of this column within the strip
+            if (F.host_rgba && x < F.W && ((relm >> j) & 1u)) F.dev_rgba[row + x] = F.host_rgba[row + x];
+            if (F.host_guide && x < F.W && ((ownm >> j) & 1u)) F.dev_guide[row + x] = F.host_guide[row + x];
+        }
+    }
+}
+
+// The shell values of the hole pixels into the caller's host shell map, after a
+// bulk copy of the whole map taken while the fill ran (its hole entries may be
+// any value of the fill's progress; every other entry was final after the init
+// pass).  One warp per strip of 8 rows x 256 columns.
+__global__ void __launch_bounds__(256) hostio_shell_fixup_kernel(const __grid_constant__ HostIOArgs a)
+{
+    if ((int)blockIdx.y >= a.n) return;
+    const HostIOFrame &F = a.f[blockIdx.y];
+    int ty, s;
+    if (!hostio_strip(F, ty, s)) return;  // warp-uniform
+    const int lane = threadIdx.x & 31;
+    const int xs = s * 32 * TILE;
+    for (int r = 0; r < TILE; r++) {
+        const int y = ty * TILE + r;
+        if (y >= F.H) break;
+        const size_t row = (size_t)y * F.W;
+#pragma unroll
+        for (int i = 0; i < 8; i++) {
+            const int x = xs + lane + 32 * i;
+            if (x < F.W && F.labels[row + x] == 1) F.host_shell[row + x] = F.dev_shell[row + x];
+        }
+    }
+}
+
+}  // namespace gf

@@ -90,6 +90,12 @@ struct FrameDev {
     int32_t *init_list;           // tiles holding part of d_active D^(0)_h (written by the init kernel)
     int32_t *init_count;          // [0] tiles on init_list, [1] |d_active D^(0)_h|
     int32_t *gleft;               // GF_FLAG_DATA: unfilled hole pixels with g != 0 (init kernel, then fills)
+    // In-place host-buffer fill (device-accessible host memory, else null): the
+    // cluster reads the colours near the holes from host_rgba before the shell
+    // loop and writes the hole pixels' colours and the whole shell map back to
+    // host_rgba / host_shell after it.
+    float4 *host_rgba;
+    int32_t *host_shell;
 };
 
 // Per-cluster control block (global memory).  Counters are indexed by the step
@@ -223,6 +229,27 @@ struct SplineChunk {
 };
 __global__ void upload_frames_kernel(const __grid_constant__ FrameChunk c);
 __global__ void upload_splines_kernel(const __grid_constant__ SplineChunk c);
+
+// Host-side inputs of the in-place host-buffer fill (gf_hostio.cu).
+struct HostIOFrame {
+    int32_t H, W, TW, TH;
+    const uint8_t *labels;        // device
+    float4 *host_rgba;            // caller's host colours (device-accessible) to gather near holes, or nullptr
+    float4 *dev_rgba;             // device working image
+    const float2 *host_guide;     // caller's host guide field (device-accessible), or nullptr
+    float2 *dev_guide;
+    uint8_t *tile_hole;           // device scratch [TW * TH]
+    const int32_t *dev_shell;     // device shell map (hostio_shell_fixup_kernel)
+    int32_t *host_shell;          // caller's host shell map (device-accessible)
+};
+constexpr int HOSTIO_MAX = 16;    // frames per launch
+struct HostIOArgs {
+    int32_t n, pad;
+    HostIOFrame f[HOSTIO_MAX];
+};
+__global__ void hostio_holes_kernel(const __grid_constant__ HostIOArgs a);
+__global__ void hostio_gather_kernel(const __grid_constant__ HostIOArgs a);
+__global__ void hostio_shell_fixup_kernel(const __grid_constant__ HostIOArgs a);
 
 // Host-side entry points of the templated fill kernel (defined beside it).
 const void *fill_kernel_entry(int rw);

@@ -226,6 +226,58 @@ def test_in_place_and_host_buffers_match():
     assert st[0]["filled"] == a["stats"]["filled"]
 
 
+@pytest.mark.parametrize("pinned", [True, False])
+def test_host_buffer_in_place_moves_only_what_the_fill_touches(pinned):
+    """In place on host buffers: pinned buffers take the sparse path (colours near
+    the holes in, hole colours out, written by the device), pageable ones full
+    copies; both leave the buffers exactly as the device-buffer fill leaves its
+    output: hole pixels filled, every other pixel untouched (NaN bystanders,
+    unreachable pixels included)."""
+    import torch
+
+    import paper_1611_05319_gb300 as gf
+    ctx = gf.context(0)
+    cases = [_case(96 + 8 * i, 136 - 5 * i, 700 + i) for i in range(5)]
+    # frame 1: a walled region (unreachable pixels keep their colour); frame 3 takes
+    # its guide field from splines
+    im, lb, g = cases[1]
+    lb = lb.copy()
+    lb[10:19, 10:19] = 2
+    lb[12:17, 12:17] = 1
+    cases[1] = (im, lb, g)
+    H3, W3 = cases[3][1].shape
+    spl = {3: (np.array([0, 3], np.int32), np.array([[2.0, 2.0], [W3 / 2.0, H3 / 2.0], [W3 - 3.0, H3 - 3.0]],
+                                                     np.float32))}
+    dev = torch.device("cuda", 0)
+    guides = [ctx.guidance(torch.from_numpy(lb).to(dev), *spl[i], 3.0).cpu().numpy() if i in spl else g
+              for i, (_, lb, g) in enumerate(cases)]
+    ref = ctx.fill_batched([torch.from_numpy(rgba(im)).to(dev) for im, _, _ in cases],
+                           [torch.from_numpy(lb).to(dev) for _, lb, _ in cases],
+                           [torch.from_numpy(np.ascontiguousarray(g, np.float32)).to(dev) for g in guides], mu=10.0)
+    torch.cuda.synchronize()
+
+    def host(a):
+        t = torch.from_numpy(np.ascontiguousarray(a))
+        return (t.pin_memory() if pinned else t.clone()).numpy()
+    bufs = [host(rgba(im)) for im, _, _ in cases]
+    before = [b.copy() for b in bufs]
+    labs = [host(lb) for _, lb, _ in cases]
+    gds = [None if i in spl else host(np.ascontiguousarray(g, np.float32)) for i, (_, _, g) in enumerate(cases)]
+    shells = [np.full(lb.shape, 9, np.int32) for _, lb, _ in cases]
+    for rep in range(2):  # a second call on the filled buffers gives the same result
+        st = ctx.fill_batched_host(bufs, labs, gds, bufs, shells, splines=[spl.get(i) for i in range(5)], eta=3.0,
+                                   mu=10.0)
+        for i, r in enumerate(ref):
+            sh = r.shell.cpu().numpy()
+            assert np.array_equal(shells[i], sh), i
+            filled = sh >= 0
+            assert np.array_equal(bufs[i][filled], r.rgba.cpu().numpy()[filled]), i
+            assert np.array_equal(np.nan_to_num(bufs[i][~filled], nan=-7.0),
+                                  np.nan_to_num(before[i][~filled], nan=-7.0)), i
+            assert st[i]["filled"] == r.stats()["filled"], i
+    assert (shells[1][12:17, 12:17] == -2).all()
+
+
 def test_repeated_calls_are_deterministic():
     d = configs.plain_128(poison=True)
     a = gpu_fill(d["rgb"], d["labels"], d["guide"])
