@@ -1362,12 +1362,14 @@ gf_status gf_fill_backward(gf_ctx *ctx, int n, const gf_adjoint_frame *frames, c
 
 }  // extern "C"
 
-// The in-place host-buffer fill on device-accessible host memory: labels and
-// polylines in, the guide fields (from the polylines, or gathered from the
-// caller's guide fields at the hole tiles), then the batched fill in the
-// context's launch shape (autotuned or set), whose kernel reads the colours near
-// the holes from the caller's buffers and writes the hole pixels' colours and the
-// shell maps back (fill kernel: host_gather, host_write_back).
+// The in-place host-buffer fill on device-accessible host memory: the labels
+// (copied in by the pass that finds the hole tiles, straight from the caller's
+// buffer where the device can address it) and polylines in; the colours of the
+// tiles within one tile of a hole tile and, for caller-given guide fields, the
+// guide of the hole tiles read from the caller's buffers (gf_hostio.cu); the
+// guide fields from the polylines; then the batched fill in the context's launch
+// shape (autotuned or set), whose clusters write each frame's hole colours back
+// into the caller's buffer when the frame is done (fill kernel: host_write_back).
 static gf_status fill_host_in_place(gf_ctx *ctx, int n, const int32_t *H, const int32_t *W,
                                     const uint8_t *const *host_labels, const int32_t *const *host_offsets,
                                     const float *const *host_pts, const int32_t *n_splines, const int32_t *n_points,
@@ -1382,10 +1384,17 @@ static gf_status fill_host_in_place(gf_ctx *ctx, int n, const int32_t *H, const 
     std::vector<gf_frame> fr(n);
     std::vector<gf_spline_frame> sf;
     std::vector<int32_t *> dev_host_shell(n, nullptr);
-    bool any_guide = false;
+    std::vector<const uint8_t *> dev_host_labels(n, nullptr);
     for (int i = 0; i < n; i++) {
         const size_t np = (size_t)H[i] * W[i];
-        CK(cudaMemcpyAsync(A + o_lab[i], host_labels[i], np, cudaMemcpyHostToDevice, st));
+        cudaPointerAttributes pa;
+        if (cudaPointerGetAttributes(&pa, host_labels[i]) == cudaSuccess && pa.type == cudaMemoryTypeHost &&
+            pa.devicePointer)
+            dev_host_labels[i] = (const uint8_t *)pa.devicePointer;
+        else {
+            cudaGetLastError();
+            CK(cudaMemcpyAsync(A + o_lab[i], host_labels[i], np, cudaMemcpyHostToDevice, st));
+        }
         if (from_splines[i] && n_splines[i] > 0) {
             CK(cudaMemcpyAsync(A + o_off[i], host_offsets[i], 4 * (size_t)(n_splines[i] + 1), cudaMemcpyHostToDevice,
                                st));
@@ -1413,46 +1422,41 @@ static gf_status fill_host_in_place(gf_ctx *ctx, int n, const int32_t *H, const 
             g.guide = (float *)(A + o_g[i]);
             g.weight = nullptr;
             sf.push_back(g);
-        } else {
-            any_guide = true;
         }
-        // the shell map goes straight into the caller's buffer when the device can
-        // address it, else through a copy after the fill
-        cudaPointerAttributes pa;
         if (cudaPointerGetAttributes(&pa, host_out_shell[i]) == cudaSuccess && pa.type == cudaMemoryTypeHost &&
             pa.devicePointer)
             dev_host_shell[i] = (int32_t *)pa.devicePointer;
         else
             cudaGetLastError();
     }
-    if (any_guide) {
-        // caller-given guide fields: those of the hole tiles, gathered by the device
-        for (int b = 0; b < n; b += HOSTIO_MAX) {
-            HostIOArgs ha;
-            memset(&ha, 0, sizeof(ha));
-            int max_tiles = 1, max_strips = 1;
-            for (int i = b; i < std::min(n, b + HOSTIO_MAX); i++) {
-                if (from_splines[i]) continue;
-                HostIOFrame &hf = ha.f[ha.n++];
-                hf.H = H[i];
-                hf.W = W[i];
-                hf.TW = (W[i] + 7) / 8;
-                hf.TH = (H[i] + 7) / 8;
-                hf.labels = (const uint8_t *)(A + o_lab[i]);
-                hf.host_guide = dev_host_guide[i];
-                hf.dev_guide = (float2 *)(A + o_g[i]);
-                hf.tile_hole = (uint8_t *)(A + o_th[i]);
-                max_tiles = std::max(max_tiles, hf.TW * hf.TH);
-                max_strips = std::max(max_strips, hf.TH * ((hf.TW + 31) / 32));
-            }
-            if (!ha.n) continue;
-            hostio_holes_kernel<<<dim3((unsigned)((max_tiles + 255) / 256), (unsigned)ha.n), 256, 0, st>>>(ha);
-            hostio_gather_kernel<<<dim3((unsigned)((max_strips + 7) / 8), (unsigned)ha.n), 256, 0, st>>>(ha);
-            CK(cudaGetLastError());
+    // hole tiles (and the labels, where the device reads them from the host), then
+    // the colours near the holes and the guide of the hole tiles
+    for (int b = 0; b < n; b += HOSTIO_MAX) {
+        HostIOArgs ha;
+        memset(&ha, 0, sizeof(ha));
+        int max_strips = 1;
+        for (int i = b; i < std::min(n, b + HOSTIO_MAX); i++) {
+            HostIOFrame &hf = ha.f[ha.n++];
+            hf.H = H[i];
+            hf.W = W[i];
+            hf.TW = (W[i] + 7) / 8;
+            hf.TH = (H[i] + 7) / 8;
+            hf.labels = (uint8_t *)(A + o_lab[i]);
+            hf.host_labels = dev_host_labels[i];
+            hf.host_rgba = dev_host_rgba[i];
+            hf.dev_rgba = (float4 *)(A + o_rgba[i]);
+            hf.host_guide = dev_host_guide[i];
+            hf.dev_guide = (float2 *)(A + o_g[i]);
+            hf.tile_hole = (uint8_t *)(A + o_th[i]);
+            max_strips = std::max(max_strips, hf.TH * ((hf.TW + 31) / 32));
         }
+        const dim3 grid((unsigned)((max_strips + 7) / 8), (unsigned)ha.n);
+        hostio_holes_kernel<<<grid, 256, 0, st>>>(ha);
+        hostio_gather_kernel<<<grid, 256, 0, st>>>(ha);
+        CK(cudaGetLastError());
     }
-    // Every colour moves inside the fill kernel.  The shell maps: where the device
-    // can address every one of them, each map is copied to the host on the copy
+    // The hole colours go back inside the fill kernel.  The shell maps: where the
+    // device can address every one of them, each map is copied to the host on the copy
     // stream as soon as the init pass has written it (every entry but the hole
     // pixels' is then final), beside the fill, and after both a small kernel
     // writes the hole pixels' final values; otherwise they are copied after the fill.
@@ -1513,7 +1517,7 @@ static gf_status fill_host_in_place(gf_ctx *ctx, int n, const int32_t *H, const 
                 hf.W = W[i];
                 hf.TW = (W[i] + 7) / 8;
                 hf.TH = (H[i] + 7) / 8;
-                hf.labels = (const uint8_t *)(A + o_lab[i]);
+                hf.labels = (uint8_t *)(A + o_lab[i]);
                 hf.dev_shell = (const int32_t *)(A + o_sh[i]);
                 hf.host_shell = dev_host_shell[i];
                 max_strips = std::max(max_strips, hf.TH * ((hf.TW + 31) / 32));

@@ -926,41 +926,6 @@ __device__ void sweep_tiles(const FillParams &p, const FrameDev &F, WarpSmem<RW>
     }
 }
 
-// In-place host-buffer fill, before the shell loop: the colours of every tile
-// within one tile of a tile holding a hole pixel (the shell loop reads colours at
-// most ceil(eps) + 1 <= 8 px from a hole pixel) from the caller's host buffer.
-// One warp per strip of 8 rows x 32 tiles; lane l on the columns l, l + 32, ...
-// of the strip, so that each access of a warp covers 512 contiguous bytes.
-__device__ void host_gather(const FrameDev &F, int gw, int nw)
-{
-    const int lane = threadIdx.x & 31;
-    const int strips = (F.TW + 31) >> 5;
-    for (int unit = gw; unit < F.TH * strips; unit += nw) {
-        const int ty = unit / strips, s = unit - ty * strips;
-        const int tx = s * 32 + lane;
-        bool rel = false;
-        if (tx < F.TW)
-            for (int dy = -1; dy <= 1; dy++)
-                for (int dx = -1; dx <= 1; dx++) {
-                    const int nx = tx + dx, ny = ty + dy;
-                    if (nx >= 0 && ny >= 0 && nx < F.TW && ny < F.TH && ld(&F.U[ny * F.TW + nx]) != 0ull) rel = true;
-                }
-        const unsigned relm = __ballot_sync(FULL, rel);
-        if (!relm) continue;
-        const int xs = s * 32 * TILE;
-        for (int r = 0; r < TILE; r++) {
-            const int y = ty * TILE + r;
-            if (y >= F.H) break;
-            const size_t row = (size_t)y * F.W;
-#pragma unroll
-            for (int i = 0; i < 8; i++) {
-                const int px = lane + 32 * i, x = xs + px;
-                if (x < F.W && ((relm >> (px >> 3)) & 1u)) F.rgba[row + x] = F.host_rgba[row + x];
-            }
-        }
-    }
-}
-
 // In-place host-buffer fill, after the shell loop: the colours of the hole
 // pixels and (where host_shell is set) the shell map of every pixel back to the
 // caller's host buffers, one row per warp at a time.
@@ -1038,10 +1003,6 @@ __global__ void __launch_bounds__(fill_warps(RW) * 32, 1) fill_kernel(const __gr
         if (threadIdx.x == 0) s_frame = p.frames[p.frame_order[p.order_first + f]];
         __syncthreads();
         const FrameDev &F = s_frame;
-        if (F.host_rgba) {
-            host_gather(F, gw, nw);
-            cluster.sync();  // the colours the shell loop reads are in place
-        }
 
         long long n_front = ld(&F.init_count[1]);
         long long filled_tot = 0, evals_tot = 0, max_front = 0;

@@ -6,9 +6,12 @@
 // writes the hole pixels' colours and the shell map back).
 //
 // Kernels (one frame per blockIdx.y, up to HOSTIO_MAX frames per launch):
-//   hostio_holes_kernel    per 8x8 tile: does it hold a hole pixel (labels)
-//   hostio_gather_kernel   host -> device guide of the hole tiles (and colours of
-//                          the tiles next to a hole tile, where host_rgba is set)
+//   hostio_holes_kernel    per 8x8 tile: does it hold a hole pixel (labels, read
+//                          from the caller's buffer where host_labels is set)
+//   hostio_gather_kernel   host -> device colours of the tiles next to a hole tile
+//                          (where host_rgba is set) and guide of the hole tiles
+//                          (where host_guide is set)
+//   hostio_shell_fixup_kernel  the hole pixels' shell values to the host
 // The gather runs one warp per strip of 8 rows x 256 columns, lane l on the
 // columns l, l + 32, ... so that every access of a warp covers contiguous bytes
 // of a row.
@@ -21,22 +24,6 @@ namespace {
 constexpr unsigned FULLM = 0xffffffffu;
 }
 
-__global__ void __launch_bounds__(256) hostio_holes_kernel(const __grid_constant__ HostIOArgs a)
-{
-    if ((int)blockIdx.y >= a.n) return;
-    const HostIOFrame &F = a.f[blockIdx.y];
-    const int t = blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= F.TW * F.TH) return;
-    const int tx = t % F.TW, ty = t / F.TW;
-    const int x0 = tx * TILE, y0 = ty * TILE;
-    bool any = false;
-    for (int r = 0; r < TILE && y0 + r < F.H; r++) {
-        const uint8_t *row = F.labels + (size_t)(y0 + r) * F.W;
-        for (int c = 0; c < TILE && x0 + c < F.W; c++) any |= row[x0 + c] == 1;
-    }
-    F.tile_hole[t] = any ? 1 : 0;
-}
-
 // The strip of warp `unit`: tile row ty, columns of tiles 32 s .. 32 s + 31.
 // Returns false (for the whole warp) past the frame's last strip.
 __device__ __forceinline__ bool hostio_strip(const HostIOFrame &F, int &ty, int &s)
@@ -47,6 +34,43 @@ __device__ __forceinline__ bool hostio_strip(const HostIOFrame &F, int &ty, int 
     ty = unit / strips;
     s = unit - ty * strips;
     return true;
+}
+
+// Per 8x8 tile: does it hold a hole pixel.  With host_labels set, the labels are
+// read from the caller's host buffer and written to the device copy on the way.
+// One warp per strip of 8 rows x 32 tiles, lane l on tile column 32 s + l.
+__global__ void __launch_bounds__(256) hostio_holes_kernel(const __grid_constant__ HostIOArgs a)
+{
+    if ((int)blockIdx.y >= a.n) return;
+    const HostIOFrame &F = a.f[blockIdx.y];
+    int ty, s;
+    if (!hostio_strip(F, ty, s)) return;  // warp-uniform
+    const int lane = threadIdx.x & 31;
+    const int tx = s * 32 + lane;
+    if (tx >= F.TW) return;
+    const int x0 = tx * TILE;
+    const uint8_t *src = F.host_labels ? F.host_labels : F.labels;
+    const bool vec = (F.W & 7) == 0 && (reinterpret_cast<uintptr_t>(src) & 7u) == 0 &&
+                     (reinterpret_cast<uintptr_t>(F.labels) & 7u) == 0;
+    bool any = false;
+    for (int r = 0; r < TILE; r++) {
+        const int y = ty * TILE + r;
+        if (y >= F.H) break;
+        const size_t o = (size_t)y * F.W + x0;
+        if (vec) {
+            const uint2 v = *reinterpret_cast<const uint2 *>(src + o);
+            if (F.host_labels) *reinterpret_cast<uint2 *>(F.labels + o) = v;
+#pragma unroll
+            for (int c = 0; c < 8; c++) any |= (((c < 4 ? v.x : v.y) >> (8 * (c & 3))) & 0xffu) == 1u;
+        } else {
+            for (int c = 0; c < TILE && x0 + c < F.W; c++) {
+                const uint8_t l = src[o + c];
+                if (F.host_labels) F.labels[o + c] = l;
+                any |= l == 1;
+            }
+        }
+    }
+    F.tile_hole[ty * F.TW + tx] = any ? 1 : 0;
 }
 
 __global__ void __launch_bounds__(256) hostio_gather_kernel(const __grid_constant__ HostIOArgs a)

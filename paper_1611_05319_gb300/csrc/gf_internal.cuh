@@ -90,10 +90,9 @@ struct FrameDev {
     int32_t *init_list;           // tiles holding part of d_active D^(0)_h (written by the init kernel)
     int32_t *init_count;          // [0] tiles on init_list, [1] |d_active D^(0)_h|
     int32_t *gleft;               // GF_FLAG_DATA: unfilled hole pixels with g != 0 (init kernel, then fills)
-    // In-place host-buffer fill (device-accessible host memory, else null): the
-    // cluster reads the colours near the holes from host_rgba before the shell
-    // loop and writes the hole pixels' colours and the whole shell map back to
-    // host_rgba / host_shell after it.
+    // In-place host-buffer fill (device-accessible host memory, else null): after
+    // the shell loop the cluster writes the hole pixels' colours (and, where
+    // host_shell is set, the whole shell map) back to the caller's buffers.
     float4 *host_rgba;
     int32_t *host_shell;
 };
@@ -233,7 +232,8 @@ __global__ void upload_splines_kernel(const __grid_constant__ SplineChunk c);
 // Host-side inputs of the in-place host-buffer fill (gf_hostio.cu).
 struct HostIOFrame {
     int32_t H, W, TW, TH;
-    const uint8_t *labels;        // device
+    uint8_t *labels;              // device
+    const uint8_t *host_labels;   // caller's host labels (device-accessible) to copy in, or nullptr
     float4 *host_rgba;            // caller's host colours (device-accessible) to gather near holes, or nullptr
     float4 *dev_rgba;             // device working image
     const float2 *host_guide;     // caller's host guide field (device-accessible), or nullptr
