@@ -415,14 +415,10 @@ int gf_max_active_clusters(gf_ctx *ctx, float eps, int cluster_size)
     return n;
 }
 
-// host_rgba / host_shell (optional, n entries each): device-accessible host
-// buffers of an in-place host-buffer fill, read and written by the fill kernel
-// itself (FrameDev::host_rgba).
 static gf_status enqueue_fill(gf_ctx *ctx, int n, const gf_frame *frames, const gf_params *prm,
                               gf_stats *dev_stats, cudaStream_t stream, cudaEvent_t ev0 = nullptr,
                               cudaEvent_t ev1 = nullptr, bool allow_graph = true, DevBuf *scratch = nullptr,
-                              cudaEvent_t wait_before_fill = nullptr, float4 *const *host_rgba = nullptr,
-                              int32_t *const *host_shell = nullptr)
+                              cudaEvent_t wait_before_fill = nullptr)
 {
     DevBuf &arena = scratch ? *scratch : ctx->arena;
     // ---- layout of the scratch arena
@@ -532,8 +528,6 @@ static gf_status enqueue_fill(gf_ctx *ctx, int n, const gf_frame *frames, const 
         d.gleft = (int32_t *)(A + off_gleft) + i;
         d.init_list = (int32_t *)(A + off_L[i]);
         d.init_count = (int32_t *)(A + off_icnt) + 2 * i;
-        if (host_rgba) d.host_rgba = host_rgba[i];
-        if (host_shell) d.host_shell = host_shell[i];
         hd[i] = d;
         hcta[i] = (int32_t)ctas;
         ctas += (int64_t)init_ctas(d.TH, f.W);
@@ -1366,10 +1360,10 @@ gf_status gf_fill_backward(gf_ctx *ctx, int n, const gf_adjoint_frame *frames, c
 // (copied in by the pass that finds the hole tiles, straight from the caller's
 // buffer where the device can address it) and polylines in; the colours of the
 // tiles within one tile of a hole tile and, for caller-given guide fields, the
-// guide of the hole tiles read from the caller's buffers (gf_hostio.cu); the
-// guide fields from the polylines; then the batched fill in the context's launch
-// shape (autotuned or set), whose clusters write each frame's hole colours back
-// into the caller's buffer when the frame is done (fill kernel: host_write_back).
+// guide of the hole tiles read from the caller's buffers, beside the guide fields
+// from the polylines and the fill's preparation; the batched fill in the
+// context's launch shape (autotuned or set); then the hole pixels' colours and
+// shell values written into the caller's buffers (gf_hostio.cu).
 static gf_status fill_host_in_place(gf_ctx *ctx, int n, const int32_t *H, const int32_t *W,
                                     const uint8_t *const *host_labels, const int32_t *const *host_offsets,
                                     const float *const *host_pts, const int32_t *n_splines, const int32_t *n_points,
@@ -1429,72 +1423,78 @@ static gf_status fill_host_in_place(gf_ctx *ctx, int n, const int32_t *H, const 
         else
             cudaGetLastError();
     }
-    // hole tiles (and the labels, where the device reads them from the host), then
-    // the colours near the holes and the guide of the hole tiles
-    for (int b = 0; b < n; b += HOSTIO_MAX) {
-        HostIOArgs ha;
-        memset(&ha, 0, sizeof(ha));
-        int max_strips = 1;
-        for (int i = b; i < std::min(n, b + HOSTIO_MAX); i++) {
-            HostIOFrame &hf = ha.f[ha.n++];
-            hf.H = H[i];
-            hf.W = W[i];
-            hf.TW = (W[i] + 7) / 8;
-            hf.TH = (H[i] + 7) / 8;
-            hf.labels = (uint8_t *)(A + o_lab[i]);
-            hf.host_labels = dev_host_labels[i];
-            hf.host_rgba = dev_host_rgba[i];
-            hf.dev_rgba = (float4 *)(A + o_rgba[i]);
-            hf.host_guide = dev_host_guide[i];
-            hf.dev_guide = (float2 *)(A + o_g[i]);
-            hf.tile_hole = (uint8_t *)(A + o_th[i]);
-            max_strips = std::max(max_strips, hf.TH * ((hf.TW + 31) / 32));
-        }
-        const dim3 grid((unsigned)((max_strips + 7) / 8), (unsigned)ha.n);
-        hostio_holes_kernel<<<grid, 256, 0, st>>>(ha);
-        hostio_gather_kernel<<<grid, 256, 0, st>>>(ha);
-        CK(cudaGetLastError());
-    }
-    // The hole colours go back inside the fill kernel.  The shell maps: where the
-    // device can address every one of them, each map is copied to the host on the copy
-    // stream as soon as the init pass has written it (every entry but the hole
-    // pixels' is then final), beside the fill, and after both a small kernel
-    // writes the hole pixels' final values; otherwise they are copied after the fill.
+    // the frames' host-side descriptors, in launches of up to HOSTIO_MAX frames
     bool all_shell = true;
     for (int i = 0; i < n; i++) all_shell = all_shell && dev_host_shell[i];
-    std::vector<float4 *> hr(dev_host_rgba.begin(), dev_host_rgba.end());
+    auto hostio = [&](int which, cudaStream_t sk) -> cudaError_t {
+        for (int b = 0; b < n; b += HOSTIO_MAX) {
+            HostIOArgs ha;
+            memset(&ha, 0, sizeof(ha));
+            int max_strips = 1;
+            for (int i = b; i < std::min(n, b + HOSTIO_MAX); i++) {
+                HostIOFrame &hf = ha.f[ha.n++];
+                hf.H = H[i];
+                hf.W = W[i];
+                hf.TW = (W[i] + 7) / 8;
+                hf.TH = (H[i] + 7) / 8;
+                hf.labels = (uint8_t *)(A + o_lab[i]);
+                hf.host_labels = dev_host_labels[i];
+                hf.host_rgba = dev_host_rgba[i];
+                hf.dev_rgba = (float4 *)(A + o_rgba[i]);
+                hf.host_guide = dev_host_guide[i];
+                hf.dev_guide = (float2 *)(A + o_g[i]);
+                hf.tile_hole = (uint8_t *)(A + o_th[i]);
+                hf.dev_shell = (const int32_t *)(A + o_sh[i]);
+                hf.host_shell = all_shell ? dev_host_shell[i] : nullptr;
+                max_strips = std::max(max_strips, hf.TH * ((hf.TW + 31) / 32));
+            }
+            const dim3 grid((unsigned)((max_strips + 7) / 8), (unsigned)ha.n);
+            if (which == 0) hostio_holes_kernel<<<grid, 256, 0, sk>>>(ha);
+            else if (which == 1) hostio_gather_kernel<<<grid, 256, 0, sk>>>(ha);
+            else hostio_write_back_kernel<<<grid, 256, 0, sk>>>(ha);
+            cudaError_t e2 = cudaGetLastError();
+            if (e2 != cudaSuccess) return e2;
+        }
+        return cudaSuccess;
+    };
+    // the hole tiles (and the labels, where the device reads them from the host)
+    CK(hostio(0, st));
     gf_stats *dst = (gf_stats *)(A + o_st);
     while ((int)ctx->pipe_ev.size() < 2) {
         cudaEvent_t ev;
         CK(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
         ctx->pipe_ev.push_back(ev);
     }
+    // the shell maps are copied on the copy stream once the init pass has written
+    // them (every entry but the hole pixels' is then final), beside the fill
     cudaEvent_t ev_init = all_shell ? ctx->pipe_ev[0] : nullptr;
     gf_status s = GF_OK;
-    if (!sf.empty() && !(params->flags & GF_FLAG_DATA)) {
-        // guide fields on the context's second stream beside the fill's preparation
+    if (!(params->flags & GF_FLAG_DATA)) {
+        // the guide fields and the colours near the holes on the context's second
+        // stream, beside the fill's preparation (descriptors, init pass, frame order)
         CK(cudaEventRecord(ctx->fork_ev, st));
         CK(cudaStreamWaitEvent(ctx->aux, ctx->fork_ev, 0));
-        s = guidance_impl(ctx, ctx->garena, (int)sf.size(), sf.data(), eta, ctx->aux);
-        if (s != GF_OK) {
+        if (!sf.empty()) s = guidance_impl(ctx, ctx->garena, (int)sf.size(), sf.data(), eta, ctx->aux);
+        cudaError_t eg = s == GF_OK ? hostio(1, ctx->aux) : cudaSuccess;
+        if (s != GF_OK || eg != cudaSuccess) {
             cudaStreamSynchronize(ctx->aux);
-            return s;
+            return s != GF_OK ? s : cuda_fail(ctx, eg);
         }
         CK(cudaEventRecord(ctx->guide_ev, ctx->aux));
-        s = enqueue_fill(ctx, n, fr.data(), params, dst, st, ev_init, nullptr, true, nullptr, ctx->guide_ev,
-                         hr.data(), nullptr);
+        s = enqueue_fill(ctx, n, fr.data(), params, dst, st, ev_init, nullptr, true, nullptr, ctx->guide_ev);
         if (s != GF_OK) {
             CK(cudaStreamWaitEvent(st, ctx->guide_ev, 0));
             cudaStreamSynchronize(st);
             return s;
         }
     } else {
+        // the init pass counts guided hole pixels: the guide fields come first
         if (!sf.empty()) {
             s = guidance_impl(ctx, ctx->garena, (int)sf.size(), sf.data(), eta, st);
             if (s != GF_OK) return s;
         }
-        s = enqueue_fill(ctx, n, fr.data(), params, dst, st, ev_init, nullptr, true, nullptr, nullptr, hr.data(),
-                         nullptr);
+        CK(hostio(1, st));
+        s = enqueue_fill(ctx, n, fr.data(), params, dst, st, ev_init, nullptr, true, nullptr, nullptr);
         if (s != GF_OK) {
             cudaStreamSynchronize(st);
             return s;
@@ -1507,28 +1507,12 @@ static gf_status fill_host_in_place(gf_ctx *ctx, int n, const int32_t *H, const 
                                ctx->copy_out));
         CK(cudaEventRecord(ctx->pipe_ev[1], ctx->copy_out));
         CK(cudaStreamWaitEvent(st, ctx->pipe_ev[1], 0));
-        for (int b = 0; b < n; b += HOSTIO_MAX) {
-            HostIOArgs ha;
-            memset(&ha, 0, sizeof(ha));
-            int max_strips = 1;
-            for (int i = b; i < std::min(n, b + HOSTIO_MAX); i++) {
-                HostIOFrame &hf = ha.f[ha.n++];
-                hf.H = H[i];
-                hf.W = W[i];
-                hf.TW = (W[i] + 7) / 8;
-                hf.TH = (H[i] + 7) / 8;
-                hf.labels = (uint8_t *)(A + o_lab[i]);
-                hf.dev_shell = (const int32_t *)(A + o_sh[i]);
-                hf.host_shell = dev_host_shell[i];
-                max_strips = std::max(max_strips, hf.TH * ((hf.TW + 31) / 32));
-            }
-            hostio_shell_fixup_kernel<<<dim3((unsigned)((max_strips + 7) / 8), (unsigned)ha.n), 256, 0, st>>>(ha);
-            CK(cudaGetLastError());
-        }
-    } else {
+    }
+    // the hole pixels' colours (and, after the bulk copy, their shell values)
+    CK(hostio(2, st));
+    if (!all_shell)
         for (int i = 0; i < n; i++)
             CK(cudaMemcpyAsync(host_out_shell[i], A + o_sh[i], 4 * (size_t)H[i] * W[i], cudaMemcpyDeviceToHost, st));
-    }
     CK(cudaMemcpyAsync(host_stats, dst, sizeof(gf_stats) * (size_t)n, cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
     return GF_OK;

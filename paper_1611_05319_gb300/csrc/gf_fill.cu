@@ -926,41 +926,6 @@ __device__ void sweep_tiles(const FillParams &p, const FrameDev &F, WarpSmem<RW>
     }
 }
 
-// In-place host-buffer fill, after the shell loop: the colours of the hole
-// pixels and (where host_shell is set) the shell map of every pixel back to the
-// caller's host buffers, one row per warp at a time.
-__device__ void host_write_back(const FrameDev &F, int gw, int nw)
-{
-    const int lane = threadIdx.x & 31;
-    const bool vec = (F.W & 3) == 0 && (reinterpret_cast<uintptr_t>(F.shell) & 15u) == 0 &&
-                     (reinterpret_cast<uintptr_t>(F.host_shell) & 15u) == 0;
-    const bool vlab = (F.W & 3) == 0 && (reinterpret_cast<uintptr_t>(F.labels) & 3u) == 0;
-    for (int y = gw; y < F.H; y += nw) {
-        const size_t row = (size_t)y * F.W;
-        if (F.host_shell && vec) {
-            const int4 *src = reinterpret_cast<const int4 *>(F.shell + row);
-            int4 *dst = reinterpret_cast<int4 *>(F.host_shell + row);
-            for (int c = lane; c < (F.W >> 2); c += 32) dst[c] = src[c];
-        } else if (F.host_shell) {
-            for (int x = lane; x < F.W; x += 32) F.host_shell[row + x] = F.shell[row + x];
-        }
-        if (vlab) {
-            const uchar4 *lab = reinterpret_cast<const uchar4 *>(F.labels + row);
-            for (int c = lane; c < (F.W >> 2); c += 32) {
-                const uchar4 l = __ldg(&lab[c]);
-                const size_t o = row + 4 * (size_t)c;
-                if (l.x == 1) F.host_rgba[o] = F.rgba[o];
-                if (l.y == 1) F.host_rgba[o + 1] = F.rgba[o + 1];
-                if (l.z == 1) F.host_rgba[o + 2] = F.rgba[o + 2];
-                if (l.w == 1) F.host_rgba[o + 3] = F.rgba[o + 3];
-            }
-        } else {
-            for (int x = lane; x < F.W; x += 32)
-                if (__ldg(&F.labels[row + x]) == 1) F.host_rgba[row + x] = F.rgba[row + x];
-        }
-    }
-}
-
 template <int RW>
 __global__ void __launch_bounds__(fill_warps(RW) * 32, 1) fill_kernel(const __grid_constant__ FillParams p)
 {
@@ -1159,8 +1124,6 @@ __global__ void __launch_bounds__(fill_warps(RW) * 32, 1) fill_kernel(const __gr
             st.status = status;
             *F.stats = st;
         }
-        // every fill of the frame happened before the loop's last cluster barrier
-        if (F.host_rgba) host_write_back(F, gw, nw);
         __syncthreads();
     }
     cp_async_wait_all();  // window copies of a last tile that had no candidates

@@ -11,7 +11,8 @@
 //   hostio_gather_kernel   host -> device colours of the tiles next to a hole tile
 //                          (where host_rgba is set) and guide of the hole tiles
 //                          (where host_guide is set)
-//   hostio_shell_fixup_kernel  the hole pixels' shell values to the host
+//   hostio_write_back_kernel   after the fill: the hole pixels' colours (and
+//                          shell values) into the caller's buffers
 // The gather runs one warp per strip of 8 rows x 256 columns, lane l on the
 // columns l, l + 32, ... so that every access of a warp covers contiguous bytes
 // of a row.
@@ -108,17 +109,21 @@ __global__ void __launch_bounds__(256) hostio_gather_kernel(const __grid_constan
     }
 }
 
-// The shell values of the hole pixels into the caller's host shell map, after a
-// bulk copy of the whole map taken while the fill ran (its hole entries may be
-// any value of the fill's progress; every other entry was final after the init
-// pass).  One warp per strip of 8 rows x 256 columns.
-__global__ void __launch_bounds__(256) hostio_shell_fixup_kernel(const __grid_constant__ HostIOArgs a)
+// After the fill: the colours of the hole pixels into the caller's host image
+// and, where host_shell is set, their shell values into the caller's host shell
+// map (which a bulk copy taken while the fill ran filled with every other entry,
+// final since the init pass).  One warp per strip of 8 rows x 256 columns.
+__global__ void __launch_bounds__(256) hostio_write_back_kernel(const __grid_constant__ HostIOArgs a)
 {
     if ((int)blockIdx.y >= a.n) return;
     const HostIOFrame &F = a.f[blockIdx.y];
     int ty, s;
     if (!hostio_strip(F, ty, s)) return;  // warp-uniform
     const int lane = threadIdx.x & 31;
+    const int tx = s * 32 + lane;
+    const bool own = tx < F.TW && F.tile_hole[ty * F.TW + tx] != 0;
+    const unsigned ownm = __ballot_sync(FULLM, own);
+    if (!ownm) return;
     const int xs = s * 32 * TILE;
     for (int r = 0; r < TILE; r++) {
         const int y = ty * TILE + r;
@@ -126,8 +131,11 @@ __global__ void __launch_bounds__(256) hostio_shell_fixup_kernel(const __grid_co
         const size_t row = (size_t)y * F.W;
 #pragma unroll
         for (int i = 0; i < 8; i++) {
-            const int x = xs + lane + 32 * i;
-            if (x < F.W && F.labels[row + x] == 1) F.host_shell[row + x] = F.dev_shell[row + x];
+            const int p = lane + 32 * i, x = xs + p;
+            if (x < F.W && ((ownm >> (p >> 3)) & 1u) && F.labels[row + x] == 1) {
+                F.host_rgba[row + x] = F.dev_rgba[row + x];
+                if (F.host_shell) F.host_shell[row + x] = F.dev_shell[row + x];
+            }
         }
     }
 }

@@ -90,11 +90,6 @@ struct FrameDev {
     int32_t *init_list;           // tiles holding part of d_active D^(0)_h (written by the init kernel)
     int32_t *init_count;          // [0] tiles on init_list, [1] |d_active D^(0)_h|
     int32_t *gleft;               // GF_FLAG_DATA: unfilled hole pixels with g != 0 (init kernel, then fills)
-    // In-place host-buffer fill (device-accessible host memory, else null): after
-    // the shell loop the cluster writes the hole pixels' colours (and, where
-    // host_shell is set, the whole shell map) back to the caller's buffers.
-    float4 *host_rgba;
-    int32_t *host_shell;
 };
 
 // Per-cluster control block (global memory).  Counters are indexed by the step
@@ -239,8 +234,8 @@ struct HostIOFrame {
     const float2 *host_guide;     // caller's host guide field (device-accessible), or nullptr
     float2 *dev_guide;
     uint8_t *tile_hole;           // device scratch [TW * TH]
-    const int32_t *dev_shell;     // device shell map (hostio_shell_fixup_kernel)
-    int32_t *host_shell;          // caller's host shell map (device-accessible)
+    const int32_t *dev_shell;     // device shell map (hostio_write_back_kernel)
+    int32_t *host_shell;          // caller's host shell map (device-accessible), or nullptr
 };
 constexpr int HOSTIO_MAX = 16;    // frames per launch
 struct HostIOArgs {
@@ -249,7 +244,7 @@ struct HostIOArgs {
 };
 __global__ void hostio_holes_kernel(const __grid_constant__ HostIOArgs a);
 __global__ void hostio_gather_kernel(const __grid_constant__ HostIOArgs a);
-__global__ void hostio_shell_fixup_kernel(const __grid_constant__ HostIOArgs a);
+__global__ void hostio_write_back_kernel(const __grid_constant__ HostIOArgs a);
 
 // Host-side entry points of the templated fill kernel (defined beside it).
 const void *fill_kernel_entry(int rw);
