@@ -489,7 +489,6 @@ static gf_status enqueue_fill(gf_ctx *ctx, int n, const gf_frame *frames, const 
     ctx->last_split_nc = snc;
     const int ncall = nc + snc;  // control blocks and work lists of both launches
 
-    const size_t off_ctl = pos; pos = align_up(pos + sizeof(GroupCtl) * (size_t)ncall, 256);
     const size_t off_lists = pos; pos = align_up(pos + 4 * (size_t)3 * list_cap * ncall, 256);
     gf_status st = ensure(ctx, arena, pos);
     if (st != GF_OK) return st;
@@ -551,14 +550,12 @@ static gf_status enqueue_fill(gf_ctx *ctx, int n, const gf_frame *frames, const 
     fp.frames = (FrameDev *)(A + off_desc);
     fp.frame_order = (int32_t *)(A + off_order);
     fp.frame_cursor = (int32_t *)(A + off_cursor);
-    fp.groups = (GroupCtl *)(A + off_ctl);
     fp.lists = (int32_t *)(A + off_lists);
     build_tab(prm->eps, fp.tab);
     FillParams fpa = fp;  // the second launch: frame_order[0 .. sm)
     fpa.n_frames = sm;
     fpa.order_first = 0;
     fpa.frame_cursor = fp.frame_cursor + 1;
-    fpa.groups = fp.groups + nc;
     fpa.lists = fp.lists + (size_t)nc * 3 * list_cap;
 
     // graph key: everything the enqueued work depends on
@@ -622,8 +619,6 @@ static gf_status enqueue_fill(gf_ctx *ctx, int n, const gf_frame *frames, const 
         if (!e) e = cudaMemsetAsync(A + off_gleft, 0, 4 * (size_t)n, stream);
         if (e) break;
         e = cudaMemsetAsync(A + off_icnt, 0, 8 * (size_t)n, stream);
-        if (e) break;
-        e = cudaMemsetAsync(A + off_ctl, 0, sizeof(GroupCtl) * (size_t)ncall, stream);
         if (e) break;
         for (int i = 0; i < n && !e; i++) {
             const gf_frame &f = frames[i];

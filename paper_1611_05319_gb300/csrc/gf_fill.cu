@@ -382,6 +382,26 @@ __device__ bool warp_ready_fp64(const FillParams &p, const WarpSmem<RW> *ws, int
     return __ddiv_rn(S_rd, S_all) > p.c64;
 }
 
+// The three work lists of a cluster (the list of step s in slot s % 3): the
+// first DS_LIST entries of each in the shared memory of the cluster's first CTA
+// (read and written by every CTA through distributed shared memory, a round trip
+// within the GPC), the rest in global memory.
+constexpr int DS_LIST = 2048;
+struct Lists {
+    int32_t *ds;    // [3][DS_LIST] in the first CTA's shared memory
+    int32_t *glob;  // [3][list_cap]; entries from DS_LIST on
+    int cap;        // list_cap
+};
+__device__ __forceinline__ void list_put(const Lists &L, int slot, int pos, int32_t v)
+{
+    if (pos < DS_LIST) L.ds[slot * DS_LIST + pos] = v;
+    else L.glob[(size_t)slot * L.cap + pos] = v;
+}
+__device__ __forceinline__ int32_t list_get(const Lists &L, int slot, int pos)
+{
+    return pos < DS_LIST ? ld(&L.ds[slot * DS_LIST + pos]) : ld(&L.glob[(size_t)slot * L.cap + pos]);
+}
+
 struct WarpCounters {
     int filled, delta, evals, err, rechecks;
 };
@@ -406,14 +426,14 @@ struct PendingClaims {
 };
 
 // Writes the reserved entries (their slot reservation has returned).
-__device__ __forceinline__ void claims_write(const FillParams &p, int32_t *lists, PendingClaims &pc, WarpCounters &wc)
+__device__ __forceinline__ void claims_write(const FillParams &p, const Lists &lists, PendingClaims &pc, WarpCounters &wc)
 {
     if (pc.m2) {  // warp-uniform
         const int lane = threadIdx.x & 31;
         const int base = __shfl_sync(FULL, pc.base2, 0);
         if ((pc.m2 >> lane) & 1u) {
             const int pos = base + __popc(pc.m2 & ((1u << lane) - 1u));
-            if (pos < p.list_cap) lists[(size_t)((pc.k + 1) % 3) * p.list_cap + pos] = pc.old2 < pc.k + 1 ? pc.nt2 : -1;
+            if (pos < p.list_cap) list_put(lists, (pc.k + 1) % 3, pos, pc.old2 < pc.k + 1 ? pc.nt2 : -1);
             else wc.err = 1;
         }
         pc.m2 = 0u;
@@ -439,7 +459,7 @@ __device__ __forceinline__ void claims_reserve(GroupCtl *ctl, PendingClaims &pc)
 }
 
 // Everything pending is written (before the step's counter flush).
-__device__ __forceinline__ void claims_drain(const FillParams &p, GroupCtl *ctl, int32_t *lists, PendingClaims &pc,
+__device__ __forceinline__ void claims_drain(const FillParams &p, GroupCtl *ctl, const Lists &lists, PendingClaims &pc,
                                              WarpCounters &wc)
 {
     claims_write(p, lists, pc, wc);
@@ -452,7 +472,7 @@ __device__ __forceinline__ void claims_drain(const FillParams &p, GroupCtl *ctl,
 // of the neighbour tiles for step k+1.
 template <int RW, int MODE>
 __device__ void process_tile(const FillParams &p, const FrameDev &F, WarpSmem<RW> *ws, GroupCtl *ctl,
-                             int32_t *lists, int t, int k, unsigned long long cand_in, WarpCounters &wc,
+                             const Lists &lists, int t, int k, unsigned long long cand_in, WarpCounters &wc,
                              PendingClaims &pc, bool defer, bool phase1)
 {
     constexpr int WS = WarpSmem<RW>::WS;
@@ -908,7 +928,7 @@ __device__ __forceinline__ void flush_counters(GroupCtl *ctl, const WarpCounters
 // Qw: stall) and is passed on as the tile's candidates.
 template <int RW, int MODE>
 __device__ void sweep_tiles(const FillParams &p, const FrameDev &F, WarpSmem<RW> *ws, GroupCtl *ctl,
-                            int32_t *lists, int k, int gw, int nw, WarpCounters &wc, PendingClaims &pc,
+                            const Lists &lists, int k, int gw, int nw, WarpCounters &wc, PendingClaims &pc,
                             bool phase1 = false)
 {
     const int lane = threadIdx.x & 31;
@@ -936,8 +956,15 @@ __global__ void __launch_bounds__(fill_warps(RW) * 32, 1) fill_kernel(const __gr
     const int crank = (int)cluster.block_rank();
     const int csize = (int)cluster.num_blocks();
     const int cid = blockIdx.x / csize;
-    GroupCtl *ctl = p.groups + cid;
-    int32_t *lists = p.lists + (size_t)cid * 3 * p.list_cap;
+    // the cluster's control block and the heads of its work lists live in the first
+    // CTA's shared memory
+    __shared__ GroupCtl s_ctl;
+    __shared__ int32_t s_lists[3 * DS_LIST];
+    GroupCtl *ctl = cluster.map_shared_rank(&s_ctl, 0);
+    Lists lists;
+    lists.ds = cluster.map_shared_rank(s_lists, 0);
+    lists.glob = p.lists + (size_t)cid * 3 * p.list_cap;
+    lists.cap = p.list_cap;
     const int gw = (threadIdx.x >> 5) * csize + crank;  // interleave CTAs
     const int nw = csize * fill_warps(RW);
     const bool leader = crank == 0 && threadIdx.x == 0;
@@ -1001,7 +1028,7 @@ __global__ void __launch_bounds__(fill_warps(RW) * 32, 1) fill_kernel(const __gr
             } else {
                 // step 0 takes the init kernel's list, later steps the lists built by the claims
                 const int n = n_cur;
-                const int32_t *L = k == 0 ? F.init_list : lists + (size_t)slot * p.list_cap;
+
                 // Item gw goes to warp gw; items beyond the warp count are handed out
                 // by a per-step cursor (the next grab is in flight while a tile is
                 // processed), so uneven tiles do not leave warps idle at the barrier.
@@ -1015,7 +1042,7 @@ __global__ void __launch_bounds__(fill_warps(RW) * 32, 1) fill_kernel(const __gr
                 if (more) {
                     int nxt = nw + __shfl_sync(FULL, pre, 0);
                     while (nxt < n) {
-                        const int t = ld(&L[nxt]);
+                        const int t = k == 0 ? ld(&F.init_list[nxt]) : list_get(lists, slot, nxt);
                         if (lane0) pre = atomicAdd(&ctl->cursor[slot], 1);
                         if (t >= 0) process_tile<RW, NORMAL>(p, F, ws, ctl, lists, t, k, 0ull, wc, pc, more, phase1);
                         nxt = nw + __shfl_sync(FULL, pre, 0);
@@ -1027,13 +1054,12 @@ __global__ void __launch_bounds__(fill_warps(RW) * 32, 1) fill_kernel(const __gr
             cluster.sync();
             // one round trip: this step's counters and the next step's list
             const int s3n = (k + 1) % 3;
-            const int32_t *Ln = lists + (size_t)s3n * p.list_cap;
             int filled = ld(&ctl->filled[slot]);
             int dlt = ld(&ctl->front_delta[slot]);
             const int ev = ld(&ctl->evals[slot]);
             const int er = ld(&ctl->err[slot]);
             int n_next = ld(&ctl->list_count[s3n]);
-            int t0_next = gw < p.list_cap ? ld(&Ln[gw]) : -1;  // used only if gw < n_next
+            int t0_next = gw < p.list_cap ? list_get(lists, s3n, gw) : -1;  // used only if gw < n_next
             const int gleft = phase1 ? ld(F.gleft) : -1;
             evals_tot += ev;
             if (er) {
@@ -1057,7 +1083,7 @@ __global__ void __launch_bounds__(fill_warps(RW) * 32, 1) fill_kernel(const __gr
                 dlt = ld(&ctl->front_delta[slot]);
                 const int er1 = ld(&ctl->err[slot]);
                 n_next = ld(&ctl->list_count[s3n]);
-                t0_next = gw < p.list_cap ? ld(&Ln[gw]) : -1;
+                t0_next = gw < p.list_cap ? list_get(lists, s3n, gw) : -1;
                 if (er1) {
                     status = GF_ERR_INTERNAL;
                     break;
@@ -1086,7 +1112,7 @@ __global__ void __launch_bounds__(fill_warps(RW) * 32, 1) fill_kernel(const __gr
                 const int er2 = ld(&ctl->err[slot]);
                 // the stall fills appended claims to the next step's list
                 n_next = ld(&ctl->list_count[s3n]);
-                t0_next = gw < p.list_cap ? ld(&Ln[gw]) : -1;
+                t0_next = gw < p.list_cap ? list_get(lists, s3n, gw) : -1;
                 if (er2) {
                     status = GF_ERR_INTERNAL;
                     break;
@@ -1127,6 +1153,9 @@ __global__ void __launch_bounds__(fill_warps(RW) * 32, 1) fill_kernel(const __gr
         __syncthreads();
     }
     cp_async_wait_all();  // window copies of a last tile that had no candidates
+    // no CTA leaves while another may still read its shared memory (the control
+    // block and list heads of the first CTA)
+    cluster.sync();
 }
 
 const void *fill_kernel_entry(int rw)

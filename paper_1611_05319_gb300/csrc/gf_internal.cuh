@@ -92,9 +92,10 @@ struct FrameDev {
     int32_t *gleft;               // GF_FLAG_DATA: unfilled hole pixels with g != 0 (init kernel, then fills)
 };
 
-// Per-cluster control block (global memory).  Counters are indexed by the step
-// that writes them (mod 3) so that no counter is reset while another CTA of the
-// cluster may still read it.
+// Per-cluster control block (in the shared memory of the cluster's first CTA,
+// used by every CTA through distributed shared memory).  Counters are indexed by
+// the step that writes them (mod 3) so that no counter is reset while another
+// CTA of the cluster may still read it.
 struct GroupCtl {
     // Per-step counters live in slot s%3 for step s.  During step s the slot of
     // step s+1 (and the work-list count of step s+2) is cleared, so a slot is
@@ -122,7 +123,6 @@ struct FillParams {
     FrameDev *frames;
     int32_t *frame_order;         // all frames of the request, largest hole first (device)
     int32_t *frame_cursor;        // this launch's work queue head
-    GroupCtl *groups;             // one per cluster
     int32_t *lists;               // [n_clusters][3][list_cap]
     SampleTab tab;
 };

@@ -46,7 +46,7 @@ constexpr int64_t NOALLOC_MAX_TILES = 66561;
 constexpr size_t up256(size_t v) { return (v + 255) / 256 * 256; }
 
 struct Layout {
-    size_t U, Q, F, S, L, holes, gleft, icnt, desc, order, cursor, ctaoff, ctl, lists, total;
+    size_t U, Q, F, S, L, holes, gleft, icnt, desc, order, cursor, ctaoff, lists, total;
 };
 
 // scratch layout of one frame with T tiles, filled by one cluster
@@ -66,7 +66,6 @@ constexpr Layout layout(int64_t T)
     l.order = p; p = up256(p + 4);
     l.cursor = p; p = up256(p + 8);  // two queue heads (order_kernel clears both)
     l.ctaoff = p; p = up256(p + 8);
-    l.ctl = p; p = up256(p + sizeof(GroupCtl));
     l.lists = p; p = up256(p + 4 * 3 * 9 * (size_t)T);  // three work lists of 9 slots per tile
     l.total = p;
     return l;
@@ -222,7 +221,6 @@ extern "C" gf_status gf_fill_noalloc(const gf_frame *f, const gf_params *p, gf_s
     fp.frames = (FrameDev *)(A + l.desc);
     fp.frame_order = (int32_t *)(A + l.order);
     fp.frame_cursor = (int32_t *)(A + l.cursor);
-    fp.groups = (GroupCtl *)(A + l.ctl);
     fp.lists = (int32_t *)(A + l.lists);
     build_tab(p->eps, fp.tab);
 
@@ -230,7 +228,6 @@ extern "C" gf_status gf_fill_noalloc(const gf_frame *f, const gf_params *p, gf_s
     if (cudaMemsetAsync(A + l.holes, 0, 4, st) != cudaSuccess) return GF_ERR_CUDA;
     if (cudaMemsetAsync(A + l.gleft, 0, 4, st) != cudaSuccess) return GF_ERR_CUDA;
     if (cudaMemsetAsync(A + l.icnt, 0, 8, st) != cudaSuccess) return GF_ERR_CUDA;
-    if (cudaMemsetAsync(A + l.ctl, 0, sizeof(GroupCtl), st) != cudaSuccess) return GF_ERR_CUDA;
     if (f->out_stall && cudaMemsetAsync(f->out_stall, 0, 4 * (((size_t)f->H * f->W + 1 + 31) / 32), st) != cudaSuccess)
         return GF_ERR_CUDA;
     if (f->out_rgba != f->rgba &&
