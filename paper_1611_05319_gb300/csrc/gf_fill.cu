@@ -60,6 +60,9 @@ __device__ __forceinline__ T ld(const T *p)
 // lanes of a pixel read different entries, which the constant cache would
 // serialise).
 __shared__ float4 g_stab[MAX_SAMPLES];
+// The same samples as mirror pairs {(n, m), (-n, -m)}: one entry per pair,
+// (n, m, 1/|(n, m)|, |m| as int bits) with m < 0, or m = 0 and n < 0.
+__shared__ float4 g_pair[MAX_SAMPLES / 2];
 
 // ---------------------------------------------------------------------------
 // init
@@ -289,18 +292,24 @@ __device__ __forceinline__ unsigned long long dilate_nbr(unsigned long long fm, 
     if (lane < 24)
         row = (uint32_t)((mL >> (8 * ry)) & 0xffu) | ((uint32_t)((mC >> (8 * ry)) & 0xffu) << 8) |
               ((uint32_t)((mR >> (8 * ry)) & 0xffu) << 16);
+    // dilation by doubling: after a pass of step st <= c + 1 a set bit covers the
+    // offsets 0 .. c + st (rows: shfl_up/down return the lane's own value at the
+    // warp's ends, and lanes 24..31 hold no row)
     uint32_t h = row;
-    for (int d = 1; d <= reach; d++) h |= (row << d) | (row >> d);
-    uint32_t hc = (lane < 24) ? ((h >> 8) & 0xffu) : 0u;
-    uint32_t v = 0;
-    for (int d = -reach; d <= reach; d++) {
-        int src = lane + 8 + d;
-        uint32_t xv = __shfl_sync(FULL, hc, src & 31);
-        if (src >= 0 && src < 24) v |= xv;
+    for (int c = 0; c < reach;) {
+        const int st = min(c + 1, reach - c);
+        h |= (h << st) | (h >> st);
+        c += st;
+    }
+    uint32_t v = (lane < 24) ? ((h >> 8) & 0xffu) : 0u;
+    for (int c = 0; c < reach;) {
+        const int st = min(c + 1, reach - c);
+        v |= __shfl_up_sync(FULL, v, st) | __shfl_down_sync(FULL, v, st);
+        c += st;
     }
     unsigned long long out = 0;
 #pragma unroll
-    for (int y = 0; y < 8; y++) out |= (unsigned long long)(__shfl_sync(FULL, v, y) & 0xffu) << (8 * y);
+    for (int y = 0; y < 8; y++) out |= (unsigned long long)(__shfl_sync(FULL, v, 8 + y) & 0xffu) << (8 * y);
     return out;
 }
 
@@ -507,12 +516,37 @@ __device__ void process_tile(const FillParams &p, const FrameDev &F, WarpSmem<RW
         }
     }
     const int wx0 = x0 - RW, wy0 = y0 - RW;
-    int32_t sv[WS];
+    // State window.  With WS = 16 a lane holds 4 columns of 2 rows (lane = 4 row +
+    // column group): one 16-byte load each when the row width is a multiple of 4 and
+    // the state array is aligned (4 columns are then wholly inside or wholly outside
+    // the frame), else 4 plain loads.  Other widths: one column per lane and row.
+    constexpr bool Q4 = WS == 16;
+    int32_t sv[Q4 ? 1 : WS];
+    int4 sq[2];
+    if (Q4) {
+        const bool vec = (W & 3) == 0 && ((uintptr_t)F.shell & 15u) == 0;
 #pragma unroll
-    for (int r = 0; r < WS; r++) {
-        int gx = wx0 + lane, gy = wy0 + r;
-        sv[r] = (lane < WS && gx >= 0 && gy >= 0 && gx < W && gy < H) ? ld(&F.shell[(size_t)gy * W + gx])
-                                                                       : SH_OUTSIDE;
+        for (int i = 0; i < 2; i++) {
+            const int gx = wx0 + 4 * (lane & 3), gy = wy0 + (lane >> 2) + 8 * i;
+            const bool rin = gy >= 0 && gy < H;
+            if (vec) {
+                sq[i] = (rin && gx >= 0 && gx < W) ? ld(reinterpret_cast<const int4 *>(&F.shell[(size_t)gy * W + gx]))
+                                                   : make_int4(SH_OUTSIDE, SH_OUTSIDE, SH_OUTSIDE, SH_OUTSIDE);
+            } else {
+                int e[4];
+#pragma unroll
+                for (int b = 0; b < 4; b++)
+                    e[b] = (rin && gx + b >= 0 && gx + b < W) ? ld(&F.shell[(size_t)gy * W + gx + b]) : SH_OUTSIDE;
+                sq[i] = make_int4(e[0], e[1], e[2], e[3]);
+            }
+        }
+    } else {
+#pragma unroll
+        for (int r = 0; r < (Q4 ? 1 : WS); r++) {
+            int gx = wx0 + lane, gy = wy0 + r;
+            sv[r] = (lane < WS && gx >= 0 && gy >= 0 && gx < W && gy < H) ? ld(&F.shell[(size_t)gy * W + gx])
+                                                                           : SH_OUTSIDE;
+        }
     }
     float2 gv[2] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
     if (MODE != STALL) {
@@ -523,10 +557,22 @@ __device__ void process_tile(const FillParams &p, const FrameDev &F, WarpSmem<RW
             if (gx < W && gy < H) gv[h] = __ldg(&F.guide[(size_t)gy * W + gx]);
         }
     }
-    for (int e = lane; e < WS * WS; e += 32) {
-        int r = e / WS, c = e - r * WS;
-        int gx = wx0 + c, gy = wy0 + r;
-        if (gx >= 0 && gy >= 0 && gx < W && gy < H) cp_async16(&ws->col[e], &F.rgba[(size_t)gy * W + gx]);
+    if (WS == 16) {
+        // lane = 16 (row parity) + column; the column test is the same for every row
+        const int c = lane & 15, r0 = lane >> 4;
+        const bool cin = (unsigned)(wx0 + c) < (unsigned)W;
+#pragma unroll
+        for (int i = 0; i < 8; i++) {
+            const int gy = wy0 + r0 + 2 * i;
+            if (cin && (unsigned)gy < (unsigned)H)
+                cp_async16(&ws->col[(r0 + 2 * i) * 16 + c], &F.rgba[(size_t)gy * W + wx0 + c]);
+        }
+    } else {
+        for (int e = lane; e < WS * WS; e += 32) {
+            int r = e / WS, c = e - r * WS;
+            int gx = wx0 + c, gy = wy0 + r;
+            if (gx >= 0 && gy >= 0 && gx < W && gy < H) cp_async16(&ws->col[e], &F.rgba[(size_t)gy * W + gx]);
+        }
     }
 
     unsigned long long cand;
@@ -543,10 +589,23 @@ __device__ void process_tile(const FillParams &p, const FrameDev &F, WarpSmem<RW
     if (cand == 0) return;
 
     // ---- readable bits of the window by ballot; guide vectors of the candidates
+    if (Q4) {
+        // each lane's 4 readable bits at column 4 (lane & 3), OR-ed over the 4 lanes of a row
 #pragma unroll
-    for (int r = 0; r < WS; r++) {
-        unsigned b = __ballot_sync(FULL, readable_at(sv[r], k));
-        if (lane == 0) ws->rowmask[r] = b;
+        for (int i = 0; i < 2; i++) {
+            uint32_t v = (readable_at(sq[i].x, k) ? 1u : 0u) | (readable_at(sq[i].y, k) ? 2u : 0u) |
+                         (readable_at(sq[i].z, k) ? 4u : 0u) | (readable_at(sq[i].w, k) ? 8u : 0u);
+            v <<= 4 * (lane & 3);
+            v |= __shfl_xor_sync(FULL, v, 1);
+            v |= __shfl_xor_sync(FULL, v, 2);
+            if ((lane & 3) == 0) ws->rowmask[(lane >> 2) + 8 * i] = v;
+        }
+    } else {
+#pragma unroll
+        for (int r = 0; r < (Q4 ? 1 : WS); r++) {
+            unsigned b = __ballot_sync(FULL, readable_at(sv[r], k));
+            if (lane == 0) ws->rowmask[r] = b;
+        }
     }
     if (MODE != STALL) {
 #pragma unroll
@@ -602,7 +661,7 @@ __device__ void process_tile(const FillParams &p, const FrameDev &F, WarpSmem<RW
         const int per = 32 / G;
         const int j = lane & (G - 1), grp = lane / G;
         const int ns = p.tab.ns;
-        const int nsp = p.tab.nsp;
+        const int npair = ns >> 1;
         const bool rot = ghost && MODE != STALL;
         const bool iso = ghost || MODE == STALL;  // the exponent depends on |m| only
         const bool fast = MODE == STALL || (ghost && smart && p.c >= 1e-30f);
@@ -638,56 +697,80 @@ __device__ void process_tile(const FillParams &p, const FrameDev &F, WarpSmem<RW
             if (act && fast) {
                 // Rotated ball under smart order, or the stall pass: the weights need no
                 // normalisation (a ready pixel has S_rd > c S_all >= c times the m = 0
-                // weights; stall weights are 1/|(n, m)|).  Branch-free, two samples per
-                // round.  Taps of zero weight and the taps of unreadable samples are read
-                // from the window's zero entry (an unreadable pixel's colour may be
-                // anything, and 0 * NaN is NaN).
+                // weights; stall weights are 1/|(n, m)|).  Branch-free, over mirror pairs
+                // {(n, m), (-n, -m)}: negation is exact and commutes with every rounding of
+                // the rotation and of the snap, so the second offset is the exact negative
+                // of the first; the pair shares its rotation, snap, floor and weights, and
+                // each tap of the second sample is the first's tap reflected through the
+                // pixel, with the same bilinear weight.  Taps of zero weight and the taps of
+                // unreadable samples are read from the window's zero entry (an unreadable
+                // pixel's colour may be anything, and 0 * NaN is NaN).
                 constexpr int ZI = WS * WS;
                 const float *eg = ws->eg[grp];
-                for (int s0 = j; s0 < nsp; s0 += 2 * G) {
-#pragma unroll
-                    for (int u = 0; u < 2; u++) {
-                        const float4 te = g_stab[s0 + u * G];  // n, m, 1/|(n, m)|, |m|
-                        const float nf = te.x, mf = te.y, invd = te.z;
-                        float ox, oy;
-                        if (rot) {
-                            ox = __fsub_rn(__fmul_rn(nf, ch), __fmul_rn(mf, sh));
-                            oy = __fadd_rn(__fmul_rn(nf, sh), __fmul_rn(mf, ch));
-                            float r0 = rintf(ox);
-                            if (fabsf(__fsub_rn(ox, r0)) <= p.tau) ox = r0;
-                            r0 = rintf(oy);
-                            if (fabsf(__fsub_rn(oy, r0)) <= p.tau) oy = r0;
-                        } else {
-                            ox = nf;
-                            oy = mf;
-                        }
-                        const float flx = floorf(ox), fly = floorf(oy);
-                        const float frx = __fsub_rn(ox, flx), fry = __fsub_rn(oy, fly);
-                        const int ix = px + RW + (int)flx, iy = py + RW + (int)fly;
-                        const bool hx = frx > 0.0f, hy = fry > 0.0f;
-                        const uint32_t need = hx ? 3u : 1u;
-                        const uint32_t rm0 = ws->rowmask[iy], rm1 = ws->rowmask[iy + 1];
-                        const bool ok = (((rm0 >> ix) & need) == need) && (!hy || (((rm1 >> ix) & need) == need));
-                        const float w0 = eg[(int)te.w] * invd;
-                        S_all += w0;
-                        S_rd += ok ? w0 : 0.f;
-                        cnt += ok ? 1 : 0;
-                        const int b0 = iy * WS + ix;
-                        const float4 v = ws->col[ok ? b0 : ZI];
-                        const float4 c1 = ws->col[ok && hx ? b0 + 1 : ZI];
-                        const float4 c2 = ws->col[ok && hy ? b0 + WS : ZI];
-                        const float4 c3 = ws->col[ok && hx && hy ? b0 + WS + 1 : ZI];
-                        const float gx = 1.f - frx, gy = 1.f - fry;
-                        const float l00 = gx * gy, l10 = frx * gy, l01 = gx * fry, l11 = frx * fry;
-                        const float vx = __fmaf_rn(l11, c3.x, __fmaf_rn(l01, c2.x, __fmaf_rn(l10, c1.x, l00 * v.x)));
-                        const float vy = __fmaf_rn(l11, c3.y, __fmaf_rn(l01, c2.y, __fmaf_rn(l10, c1.y, l00 * v.y)));
-                        const float vz = __fmaf_rn(l11, c3.z, __fmaf_rn(l01, c2.z, __fmaf_rn(l10, c1.z, l00 * v.z)));
-                        const float vw = __fmaf_rn(l11, c3.w, __fmaf_rn(l01, c2.w, __fmaf_rn(l10, c1.w, l00 * v.w)));
-                        acc.x = __fmaf_rn(w0, vx, acc.x);
-                        acc.y = __fmaf_rn(w0, vy, acc.y);
-                        acc.z = __fmaf_rn(w0, vz, acc.z);
-                        acc.w = __fmaf_rn(w0, vw, acc.w);
+                const int cx = px + RW, cy = py + RW;
+#pragma unroll 1
+                for (int q2 = j; q2 < npair; q2 += G) {
+                    const float4 te = g_pair[q2];  // n, m, 1/|(n, m)|, |m|
+                    const float nf = te.x, mf = te.y;
+                    float ox, oy;
+                    if (rot) {
+                        ox = __fsub_rn(__fmul_rn(nf, ch), __fmul_rn(mf, sh));
+                        oy = __fadd_rn(__fmul_rn(nf, sh), __fmul_rn(mf, ch));
+                        float r0 = rintf(ox);
+                        if (fabsf(__fsub_rn(ox, r0)) <= p.tau) ox = r0;
+                        r0 = rintf(oy);
+                        if (fabsf(__fsub_rn(oy, r0)) <= p.tau) oy = r0;
+                    } else {
+                        ox = nf;
+                        oy = mf;
                     }
+                    const float flx = floorf(ox), fly = floorf(oy);
+                    const float frx = __fsub_rn(ox, flx), fry = __fsub_rn(oy, fly);
+                    const int fx = (int)flx, fy = (int)fly;
+                    const bool hx = frx > 0.0f, hy = fry > 0.0f;
+                    const uint32_t need = hx ? 3u : 1u;
+                    // first sample: columns ix (+1), rows iy (+1); second: columns jx (+1)
+                    // and rows jy (-1), the reflections of the first's
+                    const int ix = cx + fx, iy = cy + fy;
+                    const int jx = cx - fx - (hx ? 1 : 0), jy = cy - fy;
+                    const uint32_t a0m = ws->rowmask[iy], a1m = ws->rowmask[iy + 1];
+                    const uint32_t b0m = ws->rowmask[jy], b1m = ws->rowmask[jy - 1];
+                    const bool ok1 = (((a0m >> ix) & need) == need) && (!hy || (((a1m >> ix) & need) == need));
+                    const bool ok2 = (((b0m >> jx) & need) == need) && (!hy || (((b1m >> jx) & need) == need));
+                    const float w0 = eg[__float_as_int(te.w)] * te.z;
+                    S_all += w0;
+                    S_all += w0;
+                    S_rd += ok1 ? w0 : 0.f;
+                    S_rd += ok2 ? w0 : 0.f;
+                    cnt += (ok1 ? 1 : 0) + (ok2 ? 1 : 0);
+                    const float gx = 1.f - frx, gy = 1.f - fry;
+                    const float l00 = w0 * (gx * gy), l10 = w0 * (frx * gy);
+                    const float l01 = w0 * (gx * fry), l11 = w0 * (frx * fry);
+                    const int A0 = iy * WS + ix, B0 = jy * WS + cx - fx;
+                    const float4 a0 = ws->col[ok1 ? A0 : ZI];
+                    const float4 a1 = ws->col[ok1 && hx ? A0 + 1 : ZI];
+                    const float4 a2 = ws->col[ok1 && hy ? A0 + WS : ZI];
+                    const float4 a3 = ws->col[ok1 && hx && hy ? A0 + WS + 1 : ZI];
+                    const float4 b0 = ws->col[ok2 ? B0 : ZI];
+                    const float4 b1 = ws->col[ok2 && hx ? B0 - 1 : ZI];
+                    const float4 b2 = ws->col[ok2 && hy ? B0 - WS : ZI];
+                    const float4 b3 = ws->col[ok2 && hx && hy ? B0 - WS - 1 : ZI];
+                    acc.x = __fmaf_rn(l00, a0.x, acc.x); acc.y = __fmaf_rn(l00, a0.y, acc.y);
+                    acc.z = __fmaf_rn(l00, a0.z, acc.z); acc.w = __fmaf_rn(l00, a0.w, acc.w);
+                    acc.x = __fmaf_rn(l10, a1.x, acc.x); acc.y = __fmaf_rn(l10, a1.y, acc.y);
+                    acc.z = __fmaf_rn(l10, a1.z, acc.z); acc.w = __fmaf_rn(l10, a1.w, acc.w);
+                    acc.x = __fmaf_rn(l01, a2.x, acc.x); acc.y = __fmaf_rn(l01, a2.y, acc.y);
+                    acc.z = __fmaf_rn(l01, a2.z, acc.z); acc.w = __fmaf_rn(l01, a2.w, acc.w);
+                    acc.x = __fmaf_rn(l11, a3.x, acc.x); acc.y = __fmaf_rn(l11, a3.y, acc.y);
+                    acc.z = __fmaf_rn(l11, a3.z, acc.z); acc.w = __fmaf_rn(l11, a3.w, acc.w);
+                    acc.x = __fmaf_rn(l00, b0.x, acc.x); acc.y = __fmaf_rn(l00, b0.y, acc.y);
+                    acc.z = __fmaf_rn(l00, b0.z, acc.z); acc.w = __fmaf_rn(l00, b0.w, acc.w);
+                    acc.x = __fmaf_rn(l10, b1.x, acc.x); acc.y = __fmaf_rn(l10, b1.y, acc.y);
+                    acc.z = __fmaf_rn(l10, b1.z, acc.z); acc.w = __fmaf_rn(l10, b1.w, acc.w);
+                    acc.x = __fmaf_rn(l01, b2.x, acc.x); acc.y = __fmaf_rn(l01, b2.y, acc.y);
+                    acc.z = __fmaf_rn(l01, b2.z, acc.z); acc.w = __fmaf_rn(l01, b2.w, acc.w);
+                    acc.x = __fmaf_rn(l11, b3.x, acc.x); acc.y = __fmaf_rn(l11, b3.y, acc.y);
+                    acc.z = __fmaf_rn(l11, b3.z, acc.z); acc.w = __fmaf_rn(l11, b3.w, acc.w);
                 }
             } else if (act) {
 #pragma unroll 2
@@ -863,13 +946,16 @@ __device__ void process_tile(const FillParams &p, const FrameDev &F, WarpSmem<RW
     //      flight; a claim lost to another tile leaves a skip marker (-1).
     if (MODE != RESCAN && Rm) {
         const int reach = R + 1;
-        uint32_t colocc = 0, rowocc = 0;
-#pragma unroll
-        for (int y = 0; y < 8; y++) {
-            uint32_t bt = (uint32_t)((Rm >> (8 * y)) & 0xffu);
-            colocc |= bt;
-            if (bt) rowocc |= 1u << y;
-        }
+        // columns holding a fill: OR of the 8 row bytes; rows holding one: bit 8y of
+        // the byte-wise OR, gathered into bit y by the multiply
+        unsigned long long cb = Rm | (Rm >> 32);
+        cb |= cb >> 16;
+        cb |= cb >> 8;
+        const uint32_t colocc = (uint32_t)(cb & 0xffu);
+        unsigned long long rb = Rm | (Rm >> 4);
+        rb |= rb >> 2;
+        rb |= rb >> 1;
+        const uint32_t rowocc = (uint32_t)(((rb & 0x0101010101010101ull) * 0x0102040810204080ull) >> 56);
         const uint32_t lowm = reach >= 8 ? 0xffu : ((1u << reach) - 1u);
         const bool nL = (colocc & lowm) != 0, nR = (colocc >> (8 - (reach >= 8 ? 8 : reach))) != 0;
         const bool nU = (rowocc & lowm) != 0, nD = (rowocc >> (8 - (reach >= 8 ? 8 : reach))) != 0;
@@ -969,8 +1055,19 @@ __global__ void __launch_bounds__(fill_warps(RW) * 32, 1) fill_kernel(const __gr
     const int nw = csize * fill_warps(RW);
     const bool leader = crank == 0 && threadIdx.x == 0;
     const bool rescan = (p.flags & GF_FLAG_RESCAN) != 0;
-    for (int i = threadIdx.x; i < p.tab.nsp; i += blockDim.x)
+    for (int i = threadIdx.x; i < p.tab.nsp; i += blockDim.x) {
         g_stab[i] = make_float4(p.tab.n_f[i], p.tab.m_f[i], p.tab.invd[i], fabsf(p.tab.m_f[i]));
+        // group |m| = g lists m = -g before m = +g (n ascending within each), and
+        // n < 0 before n > 0 for g = 0: the first half of every group holds one
+        // sample of each mirror pair, and every group before it has an even count
+        if (i < p.tab.ns) {
+            const int g = (int)fabsf(p.tab.m_f[i]);
+            const int g0 = p.tab.m_start[g], half = (p.tab.m_start[g + 1] - g0) >> 1;
+            if (i - g0 < half)
+                g_pair[(g0 >> 1) + (i - g0)] =
+                    make_float4(p.tab.n_f[i], p.tab.m_f[i], p.tab.invd[i], __int_as_float(g));
+        }
+    }
     if ((threadIdx.x & 31) == 0) ws->col[WarpSmem<RW>::WS * WarpSmem<RW>::WS] = make_float4(0.f, 0.f, 0.f, 0.f);
     __syncthreads();
 
