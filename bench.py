@@ -42,15 +42,15 @@ WORKLOAD = ("batched: 64 frames 1920x1080 RGBA fp32 (seeds 100-163), holes U[0.5
 SEED0, NFRAMES = 100, 64
 
 # DRAM traffic of fill_kernel per filled pixel from the ncu capture of the first 8
-# frames of this batch (dram__bytes_read.sum + dram__bytes_write.sum = 36.3904 MB +
-# 0.653568 MB for 534,164 filled pixels).  It holds only for the kernel sources it
+# frames of this batch (dram__bytes_read.sum + dram__bytes_write.sum = 36.40576 MB +
+# 0.742144 MB for 534,164 filled pixels).  It holds only for the kernel sources it
 # was taken on: with any other source the roofline's traffic is reported as null.
 FILL_TRAFFIC = {
     "sources": {
-        "paper_1611_05319_gb300/csrc/gf_fill.cu": "6388e7e478e05f0e2e432b3152802ea6bdd3fd45a8be07da001e8ac82f37a04e",
-        "paper_1611_05319_gb300/csrc/gf_internal.cuh": "f78a44b9ab487dd672ac86df35df35e2f7986e3d9fff779de3db33fb1a304ce4",
+        "paper_1611_05319_gb300/csrc/gf_fill.cu": "3c32c47896bde25f6dce787fdfb7de9375b884b09ea4de027cedc3396bf10c22",
+        "paper_1611_05319_gb300/csrc/gf_internal.cuh": "b8107c4345fb3bc9b46c283adb8c38784e612a4479870e0e3039a9a68cc44989",
     },
-    "bytes_per_filled_px": (36.3904e6 + 0.653568e6) / 534164,
+    "bytes_per_filled_px": (36.40576e6 + 0.742144e6) / 534164,
 }
 
 
