@@ -384,10 +384,11 @@ gf_status gf_get_last_split(const gf_ctx *ctx, int *split_m, int *cluster_size, 
 /*
  * Autotuner (no counterpart in the paper): fills these frames under every
  * schedulable cluster size (1, 2, 4, 8, 16 CTAs per frame, as many persistent
- * clusters as fit), then under split schedules (the m = 1, 2, 4, 8, 12, 16, 24
- * largest holes on m or m/2 clusters of 8 or 16 CTAs beside the best uniform
- * launch), `trials`
- * timed runs each (CUDA events around the fill), and records the fastest
+ * clusters as fit), then under split schedules (the m = 1..8, 10, 12, 14, 16,
+ * 20, 24 largest holes on m, 3m/4 or m/2 clusters of 8 or 16 CTAs beside the
+ * best uniform launch, then split sizes and cluster counts within 2 of the best
+ * split), `trials` timed runs each (CUDA events around the fill; about a hundred
+ * schedules in all), and records the fastest
  * schedule in the context for later automatic fills of frames with the same
  * sizes, count, flags and ceil(eps).  The frames are filled by every trial.
  * Synchronises `stream`.  Optional outputs: the chosen cluster size of the main

@@ -725,8 +725,9 @@ gf_status gf_fill_batched(gf_ctx *ctx, int n, const gf_frame *frames, const gf_p
 /* Times the batched fill of these frames under candidate launch shapes and keeps
  * the fastest for later calls on frames of the same sizes and parameters:
  * uniform schedules (cluster sizes 1..16, as many clusters as fit), then split
- * schedules (the m = 1, 2, 4, 8, 12, 16, 24 largest holes on m or m/2 clusters
- * of 8 or 16 CTAs beside the best uniform launch).  The frames are filled (in place if
+ * schedules (the m = 1..8, 10, 12, 14, 16, 20, 24 largest holes on m, 3m/4 or m/2
+ * clusters of 8 or 16 CTAs beside the best uniform launch, then the split sizes and
+ * cluster counts within 2 of the best split).  The frames are filled (in place if
  * out_rgba == rgba) by every trial.  Synchronises stream. */
 gf_status gf_autotune(gf_ctx *ctx, int n, const gf_frame *frames, const gf_params *params, gf_stats *dev_stats,
                       void *stream, int trials, int *best_cluster_size, float *best_ms)
@@ -782,32 +783,43 @@ gf_status gf_autotune(gf_ctx *ctx, int n, const gf_frame *frames, const gf_param
     }
     // split schedules: the frames with the largest holes (whose shell chains are
     // usually the longest) on a few larger clusters, the rest on the best uniform
-    // cluster size with the SMs left over
+    // cluster size with the SMs left over.  The batch time is not smooth in the
+    // split (the dynamic queue of each launch decides when the long frames start),
+    // so a coarse grid is followed by the neighbours of its best point.
     if (s == GF_OK && best_cs > 0 && n > 1) {
         ctx->cluster_size = best_cs;
         ctx->n_clusters = 0;
-        for (int m : {1, 2, 4, 8, 12, 16, 24}) {
-            if (m >= n || s != GF_OK) break;
+        auto trial = [&](int m, int scs, int snc) {
+            if (s != GF_OK || m < 1 || m >= n || snc < 1 || snc > m || scs <= best_cs) return;
+            if (snc * scs > ctx->sm_count - best_cs) return;
+            ctx->split_m = m;
+            ctx->split_cs = scs;
+            ctx->split_nc = snc;
+            float avg = 0.f;
+            s = measure(&avg);
+            if (s != GF_OK) return;
+            if (ctx->last_split_m == m && avg < best) {
+                best = avg;
+                best_nc = ctx->last_n_clusters;
+                best_sm = m;
+                best_scs = scs;
+                best_snc = ctx->last_split_nc;
+            }
+        };
+        for (int m : {1, 2, 3, 4, 5, 6, 7, 8, 10, 12, 14, 16, 20, 24}) {
             for (int scs : {8, 16}) {
-                if (scs <= best_cs || s != GF_OK) continue;
-                const int cands[2] = {m, (m + 1) / 2};
-                for (int ci = 0; ci < (cands[1] == cands[0] ? 1 : 2); ci++) {
-                    const int snc = cands[ci];
-                    ctx->split_m = m;
-                    ctx->split_cs = scs;
-                    ctx->split_nc = snc;
-                    float avg = 0.f;
-                    s = measure(&avg);
-                    if (s != GF_OK) break;
-                    if (ctx->last_split_m == m && avg < best) {
-                        best = avg;
-                        best_nc = ctx->last_n_clusters;
-                        best_sm = m;
-                        best_scs = scs;
-                        best_snc = ctx->last_split_nc;
-                    }
+                const int cands[3] = {m, (3 * m + 3) / 4, (m + 1) / 2};
+                for (int ci = 0; ci < 3; ci++) {
+                    if (ci > 0 && cands[ci] == cands[ci - 1]) continue;
+                    trial(m, scs, cands[ci]);
                 }
             }
+        }
+        if (best_sm > 0) {
+            const int m0 = best_sm, scs0 = best_scs, snc0 = best_snc;
+            for (int dm = -2; dm <= 2; dm++)
+                for (int dc = -2; dc <= 2; dc++)
+                    if (dm != 0 || dc != 0) trial(m0 + dm, scs0, snc0 + dc);
         }
     }
     if (s != GF_OK) return s;
