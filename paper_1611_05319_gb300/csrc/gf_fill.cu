@@ -248,24 +248,6 @@ __global__ void order_kernel(const FrameDev *frames, int n, int32_t *order, int3
 // which the data term of eq. ready2 is switched off), with claims.
 enum Mode { NORMAL = 0, RESCAN = 1, STALL = 2, REVAL = 3 };
 
-__device__ __forceinline__ int nth_bit64(unsigned long long m, int q)
-{
-    int pos = 0;
-#pragma unroll
-    for (int w = 32; w >= 1; w >>= 1) {
-        unsigned long long low = m & ((1ull << w) - 1ull);
-        int c = __popcll(low);
-        if (q >= c) {
-            q -= c;
-            m >>= w;
-            pos += w;
-        } else {
-            m = low;
-        }
-    }
-    return pos;
-}
-
 __device__ __forceinline__ void cp_async16(void *smem, const void *gmem)
 {
     unsigned s = (unsigned)__cvta_generic_to_shared(smem);
@@ -647,6 +629,12 @@ __device__ void process_tile(const FillParams &p, const FrameDev &F, WarpSmem<RW
     }
     const int np = __popcll(P);
     wc.evals += np;
+    // the front pixels in increasing order: pixel q of a pass is plist[q]
+#pragma unroll
+    for (int h = 0; h < 2; h++) {
+        const int pix = lane + 32 * h;
+        if ((P >> pix) & 1ull) ws->plist[__popcll(P & ((1ull << pix) - 1ull))] = (uint8_t)pix;
+    }
 
     // ---- ready test (eqs. weight, confidence, ready) and the fill value in one
     //      pass over the samples, G lanes per front pixel.  Each lane keeps its
@@ -668,7 +656,7 @@ __device__ void process_tile(const FillParams &p, const FrameDev &F, WarpSmem<RW
         for (int base = 0; base < np; base += per) {
             const int q = base + grp;
             const bool act = q < np;
-            const int pix = act ? nth_bit64(P, q) : 0;
+            const int pix = act ? ws->plist[q] : 0;
             const int px = pix & 7, py = pix >> 3;
             float2 g = make_float2(0.f, 0.f);
             if (act && MODE != STALL) g = ws->guide[pix];

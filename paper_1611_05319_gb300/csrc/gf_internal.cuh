@@ -62,6 +62,7 @@ struct WarpSmem {
     float eg[32][MAX_R + 1];     // per pixel slot of a pass: e^(-beta g^2) for g = |m| = 0..R
     unsigned long long ready;
     unsigned long long recheck;   // pixels whose ready test is re-done in FP64
+    uint8_t plist[64];           // the tile's front pixels in increasing order
 };
 
 struct TileF {                    // fills of one tile at one step
