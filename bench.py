@@ -42,15 +42,15 @@ WORKLOAD = ("batched: 64 frames 1920x1080 RGBA fp32 (seeds 100-163), holes U[0.5
 SEED0, NFRAMES = 100, 64
 
 # DRAM traffic of fill_kernel per filled pixel from the ncu capture of the first 8
-# frames of this batch (dram__bytes_read.sum + dram__bytes_write.sum = 36.40576 MB +
-# 0.742144 MB for 534,164 filled pixels).  It holds only for the kernel sources it
+# frames of this batch (dram__bytes_read.sum + dram__bytes_write.sum = 36.405248 MB +
+# 0.703488 MB for 534,164 filled pixels).  It holds only for the kernel sources it
 # was taken on: with any other source the roofline's traffic is reported as null.
 FILL_TRAFFIC = {
     "sources": {
-        "paper_1611_05319_gb300/csrc/gf_fill.cu": "3c32c47896bde25f6dce787fdfb7de9375b884b09ea4de027cedc3396bf10c22",
-        "paper_1611_05319_gb300/csrc/gf_internal.cuh": "b8107c4345fb3bc9b46c283adb8c38784e612a4479870e0e3039a9a68cc44989",
+        "paper_1611_05319_gb300/csrc/gf_fill.cu": "05bd7fef7a46742afda78a39f03380b4b2735f0ba61a189ddd68de81aba5e52d",
+        "paper_1611_05319_gb300/csrc/gf_internal.cuh": "579503f8a6004f3781209f5e368b88004acaff028e80e2431b92119d6a10f3c1",
     },
-    "bytes_per_filled_px": (36.40576e6 + 0.742144e6) / 534164,
+    "bytes_per_filled_px": (36.405248e6 + 0.703488e6) / 534164,
 }
 
 
