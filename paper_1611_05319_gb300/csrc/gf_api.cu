@@ -633,6 +633,9 @@ static gf_status enqueue_fill(gf_ctx *ctx, int n, const gf_frame *frames, const 
         ia.cta_offset = (const int32_t *)(A + off_ctaoff);
         ia.n_frames = n;
         ia.flags = prm->flags;
+        ia.uniform_ctas = hcta[1] - hcta[0];
+        for (int i = 1; i < n; i++)
+            if (hcta[i + 1] - hcta[i] != ia.uniform_ctas) ia.uniform_ctas = 0;
         init_kernel<<<(unsigned)ctas, 32 * INIT_WARPS, 0, stream>>>(ia);
         e = cudaGetLastError();
         if (e) break;

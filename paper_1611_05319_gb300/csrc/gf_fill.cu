@@ -92,29 +92,35 @@ __device__ __forceinline__ void init_label_row(const uint8_t *labels, int W, int
             v.y = b[4] | (b[5] << 8) | (b[6] << 16) | (b[7] << 24);
         }
     }
-    uint32_t k = 0, h = 0;
-#pragma unroll
-    for (int c = 0; c < 8; c++) {
-        const uint32_t l = ((c < 4 ? v.x : v.y) >> (8 * (c & 3))) & 0xffu;
-        k |= (uint32_t)(l == 0) << c;
-        h |= (uint32_t)(l == 1) << c;
-    }
-    kn = k;
-    ho = h;
+    // four labels at a time: __vseteq4 sets bit 8i of a word where byte i matches, and
+    // the multiply gathers bits 0, 8, 16, 24 into bits 21..24 (the partial products
+    // 2^(8i + 7j) are distinct, so nothing carries)
+    auto bits4 = [](uint32_t x) { return ((x * 0x00204081u) >> 21) & 0xfu; };
+    kn = bits4(__vseteq4(v.x, 0u)) | (bits4(__vseteq4(v.y, 0u)) << 4);
+    ho = bits4(__vseteq4(v.x, 0x01010101u)) | (bits4(__vseteq4(v.y, 0x01010101u)) << 4);
 }
 
-__global__ void __launch_bounds__(32 * INIT_WARPS) init_kernel(const __grid_constant__ InitArgs a)
+__global__ void __launch_bounds__(32 * INIT_WARPS, 5) init_kernel(const __grid_constant__ InitArgs a)
 {
     const int b = blockIdx.x;
-    int lo = 0, hi = a.n_frames;  // frame f with cta_offset[f] <= b < cta_offset[f+1]
-    while (hi - lo > 1) {
-        int mid = (lo + hi) >> 1;
-        if (__ldg(&a.cta_offset[mid]) <= b) lo = mid; else hi = mid;
+    // frame f with cta_offset[f] <= b < cta_offset[f+1] (a division when every frame
+    // takes the same number of CTAs)
+    int lo = 0, first = 0;
+    if (a.uniform_ctas > 0) {
+        lo = b / a.uniform_ctas;
+        first = lo * a.uniform_ctas;
+    } else {
+        int hi = a.n_frames;
+        while (hi - lo > 1) {
+            int mid = (lo + hi) >> 1;
+            if (__ldg(&a.cta_offset[mid]) <= b) lo = mid; else hi = mid;
+        }
+        first = __ldg(&a.cta_offset[lo]);
     }
     const FrameDev &F = a.frames[lo];
     const int H = F.H, W = F.W, TW = F.TW, TH = F.TH;
     const int strips = (TW + 31) >> 5;
-    const int unit = (b - __ldg(&a.cta_offset[lo])) * INIT_WARPS + (threadIdx.x >> 5);
+    const int unit = (b - first) * INIT_WARPS + (threadIdx.x >> 5);
     if (unit >= TH * strips) return;  // warp-uniform
     const int lane = threadIdx.x & 31;
     const int ty = unit / strips, sx = unit - ty * strips;
@@ -159,7 +165,9 @@ __global__ void __launch_bounds__(32 * INIT_WARPS) init_kernel(const __grid_cons
         int32_t sw[8], en[8];
 #pragma unroll
         for (int c = 0; c < 8; c++) {
-            sw[c] = ((known >> c) & 1u) ? SH_KNOWN : (((urow >> c) & 1u) ? SH_UNFILLED : SH_BYST);
+            // known and hole exclude each other
+            static_assert(SH_KNOWN == SH_BYST + 2 && SH_UNFILLED == SH_BYST + 1, "state word values");
+            sw[c] = SH_BYST + 2 * (int32_t)((known >> c) & 1u) + (int32_t)((urow >> c) & 1u);
             en[c] = ((qrow >> c) & 1u) ? 0 : -1;
         }
         const size_t o = (size_t)y * W + x0;
@@ -193,8 +201,10 @@ __global__ void __launch_bounds__(32 * INIT_WARPS) init_kernel(const __grid_cons
         F.U[t] = U;
         F.Qw[t] = Q;
         F.sched[t] = -1;
-        F.F[t].tag = INT32_MIN;
-        F.F[F.ntiles + t].tag = INT32_MIN;
+        // both fill records whole (mask 0, tag INT32_MIN): 16-byte stores leave no
+        // partially written L2 sector to be read back from DRAM
+        reinterpret_cast<int4 *>(&F.F[t])[0] = make_int4(0, 0, INT32_MIN, 0);
+        reinterpret_cast<int4 *>(&F.F[F.ntiles + t])[0] = make_int4(0, 0, INT32_MIN, 0);
     }
     const int holes = __reduce_add_sync(FULL, __popcll(U));
     const int nq = __reduce_add_sync(FULL, __popcll(Q));

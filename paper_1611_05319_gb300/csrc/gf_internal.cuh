@@ -134,6 +134,7 @@ struct InitArgs {
     const int32_t *cta_offset;
     int32_t n_frames;
     uint32_t flags;
+    int32_t uniform_ctas;         // CTAs of every frame when all frames take the same number, else 0
 };
 
 // guide-field sampler

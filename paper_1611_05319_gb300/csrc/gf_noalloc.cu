@@ -240,6 +240,7 @@ extern "C" gf_status gf_fill_noalloc(const gf_frame *f, const gf_params *p, gf_s
     ia.frames = fp.frames;
     ia.cta_offset = (const int32_t *)(A + l.ctaoff);
     ia.n_frames = 1;
+    ia.uniform_ctas = 0;
     ia.flags = p->flags;
     init_kernel<<<(unsigned)ch.cta[1], 32 * INIT_WARPS, 0, st>>>(ia);
     order_kernel<<<1, 256, 0, st>>>(fp.frames, 1, fp.frame_order, fp.frame_cursor);
