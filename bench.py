@@ -42,15 +42,15 @@ WORKLOAD = ("batched: 64 frames 1920x1080 RGBA fp32 (seeds 100-163), holes U[0.5
 SEED0, NFRAMES = 100, 64
 
 # DRAM traffic of fill_kernel per filled pixel from the ncu capture of the first 8
-# frames of this batch (dram__bytes_read.sum + dram__bytes_write.sum = 36.405248 MB +
-# 0.703488 MB for 534,164 filled pixels).  It holds only for the kernel sources it
+# frames of this batch (dram__bytes_read.sum + dram__bytes_write.sum = 36.384512 MB +
+# 0.675584 MB for 534,164 filled pixels).  It holds only for the kernel sources it
 # was taken on: with any other source the roofline's traffic is reported as null.
 FILL_TRAFFIC = {
     "sources": {
-        "paper_1611_05319_gb300/csrc/gf_fill.cu": "05bd7fef7a46742afda78a39f03380b4b2735f0ba61a189ddd68de81aba5e52d",
-        "paper_1611_05319_gb300/csrc/gf_internal.cuh": "579503f8a6004f3781209f5e368b88004acaff028e80e2431b92119d6a10f3c1",
+        "paper_1611_05319_gb300/csrc/gf_fill.cu": "53f6347da3022ebd284ebd39c39f5e8bfe24cf1baea65842f4d27eb6205363de",
+        "paper_1611_05319_gb300/csrc/gf_internal.cuh": "6594df5bed210caf9ed1e4239994c6eefc103d6780be7b7723193423c4c422f3",
     },
-    "bytes_per_filled_px": (36.405248e6 + 0.703488e6) / 534164,
+    "bytes_per_filled_px": (36.384512e6 + 0.675584e6) / 534164,
 }
 
 
