@@ -15,7 +15,9 @@
 //                          shell values) into the caller's buffers
 // The gather runs one warp per strip of 8 rows x 256 columns, lane l on the
 // columns l, l + 32, ... so that every access of a warp covers contiguous bytes
-// of a row.
+// of a row.  Every kernel issues a batch of loads before the stores that use them:
+// a store may alias a later load, so the compiler keeps program order, and
+// alternating loads and stores would leave one host round trip in flight per warp.
 
 #include "gf_internal.cuh"
 
@@ -54,16 +56,27 @@ __global__ void __launch_bounds__(256) hostio_holes_kernel(const __grid_constant
     const bool vec = (F.W & 7) == 0 && (reinterpret_cast<uintptr_t>(src) & 7u) == 0 &&
                      (reinterpret_cast<uintptr_t>(F.labels) & 7u) == 0;
     bool any = false;
-    for (int r = 0; r < TILE; r++) {
-        const int y = ty * TILE + r;
-        if (y >= F.H) break;
-        const size_t o = (size_t)y * F.W + x0;
-        if (vec) {
-            const uint2 v = *reinterpret_cast<const uint2 *>(src + o);
-            if (F.host_labels) *reinterpret_cast<uint2 *>(F.labels + o) = v;
+    if (vec) {
+        // the tile's 8 rows in flight together
+        uint2 v[TILE];
 #pragma unroll
-            for (int c = 0; c < 8; c++) any |= (((c < 4 ? v.x : v.y) >> (8 * (c & 3))) & 0xffu) == 1u;
-        } else {
+        for (int r = 0; r < TILE; r++) {
+            const int y = ty * TILE + r;
+            v[r] = y < F.H ? *reinterpret_cast<const uint2 *>(src + (size_t)y * F.W + x0) : make_uint2(0u, 0u);
+        }
+#pragma unroll
+        for (int r = 0; r < TILE; r++) {
+            const int y = ty * TILE + r;
+            if (y >= F.H) break;
+            if (F.host_labels) *reinterpret_cast<uint2 *>(F.labels + (size_t)y * F.W + x0) = v[r];
+#pragma unroll
+            for (int c = 0; c < 8; c++) any |= (((c < 4 ? v[r].x : v[r].y) >> (8 * (c & 3))) & 0xffu) == 1u;
+        }
+    } else {
+        for (int r = 0; r < TILE; r++) {
+            const int y = ty * TILE + r;
+            if (y >= F.H) break;
+            const size_t o = (size_t)y * F.W + x0;
             for (int c = 0; c < TILE && x0 + c < F.W; c++) {
                 const uint8_t l = src[o + c];
                 if (F.host_labels) F.labels[o + c] = l;
@@ -95,16 +108,27 @@ __global__ void __launch_bounds__(256) hostio_gather_kernel(const __grid_constan
     const unsigned relm = __ballot_sync(FULLM, rel), ownm = __ballot_sync(FULLM, own);
     if (!relm) return;
     const int xs = s * 32 * TILE;
-    for (int r = 0; r < TILE; r++) {
-        const int y = ty * TILE + r;
-        if (y >= F.H) break;
-        const size_t row = (size_t)y * F.W;
+    // two rows (16 colours a lane) in flight at a time
+    for (int r0 = 0; r0 < TILE; r0 += 2) {
+        float4 c[16];
+        float2 g[16];
 #pragma unroll
-        for (int i = 0; i < 8; i++) {
-            const int p = lane + 32 * i, x = xs + p;
-            const int j = p >> 3;  // tile of this column within the strip
-            if (F.host_rgba && x < F.W && ((relm >> j) & 1u)) F.dev_rgba[row + x] = F.host_rgba[row + x];
-            if (F.host_guide && x < F.W && ((ownm >> j) & 1u)) F.dev_guide[row + x] = F.host_guide[row + x];
+        for (int k = 0; k < 16; k++) {
+            const int y = ty * TILE + r0 + (k >> 3), p = lane + 32 * (k & 7), x = xs + p;
+            const size_t o = (size_t)y * F.W + x;
+            const bool in = y < F.H && x < F.W;
+            c[k] = make_float4(0.f, 0.f, 0.f, 0.f);
+            g[k] = make_float2(0.f, 0.f);
+            if (F.host_rgba && in && ((relm >> (p >> 3)) & 1u)) c[k] = F.host_rgba[o];
+            if (F.host_guide && in && ((ownm >> (p >> 3)) & 1u)) g[k] = F.host_guide[o];
+        }
+#pragma unroll
+        for (int k = 0; k < 16; k++) {
+            const int y = ty * TILE + r0 + (k >> 3), p = lane + 32 * (k & 7), x = xs + p;
+            const size_t o = (size_t)y * F.W + x;
+            const bool in = y < F.H && x < F.W;
+            if (F.host_rgba && in && ((relm >> (p >> 3)) & 1u)) F.dev_rgba[o] = c[k];
+            if (F.host_guide && in && ((ownm >> (p >> 3)) & 1u)) F.dev_guide[o] = g[k];
         }
     }
 }
@@ -129,12 +153,28 @@ __global__ void __launch_bounds__(256) hostio_write_back_kernel(const __grid_con
         const int y = ty * TILE + r;
         if (y >= F.H) break;
         const size_t row = (size_t)y * F.W;
+        // the row's labels, then its hole colours and shell values, all loaded before
+        // the host stores
+        bool h[8];
 #pragma unroll
         for (int i = 0; i < 8; i++) {
             const int p = lane + 32 * i, x = xs + p;
-            if (x < F.W && ((ownm >> (p >> 3)) & 1u) && F.labels[row + x] == 1) {
-                F.host_rgba[row + x] = F.dev_rgba[row + x];
-                if (F.host_shell) F.host_shell[row + x] = F.dev_shell[row + x];
+            h[i] = x < F.W && ((ownm >> (p >> 3)) & 1u) && F.labels[row + x] == 1;
+        }
+        float4 c[8];
+        int32_t sh[8];
+#pragma unroll
+        for (int i = 0; i < 8; i++) {
+            const size_t o = row + xs + lane + 32 * i;
+            c[i] = h[i] ? F.dev_rgba[o] : make_float4(0.f, 0.f, 0.f, 0.f);
+            sh[i] = (h[i] && F.host_shell) ? F.dev_shell[o] : 0;
+        }
+#pragma unroll
+        for (int i = 0; i < 8; i++) {
+            const size_t o = row + xs + lane + 32 * i;
+            if (h[i]) {
+                F.host_rgba[o] = c[i];
+                if (F.host_shell) F.host_shell[o] = sh[i];
             }
         }
     }
