@@ -25,6 +25,8 @@ struct gf_ctx {
     DevBuf arena;       // fill scratch
     DevBuf garena;      // guidance scratch
     DevBuf io;          // host-buffer path device copies
+    void *hstage = nullptr;   // pinned staging of the host-buffer path's splines
+    size_t hstage_bytes = 0;
     DevBuf aarena;      // adjoint scratch
     DevBuf darena;      // spline-detection scratch
     // cached graphs of the last batched fill: gexec = preparation (descriptor
@@ -304,7 +306,13 @@ gf_status gf_create(gf_ctx **out, int device)
         }
     }
     e = cudaStreamCreateWithFlags(&ctx->aux, cudaStreamNonBlocking);
-    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&ctx->copy_in, cudaStreamNonBlocking);
+    if (e == cudaSuccess) {
+        // highest priority: the host-buffer gather on this stream takes SMs ahead of
+        // the guide kernel's large grid beside it
+        int lo = 0, hi = 0;
+        e = cudaDeviceGetStreamPriorityRange(&lo, &hi);
+        if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&ctx->copy_in, cudaStreamNonBlocking, hi);
+    }
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&ctx->copy_out, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->fork_ev, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->join_ev, cudaEventDisableTiming);
@@ -324,6 +332,7 @@ void gf_destroy(gf_ctx *ctx)
     cudaSetDevice(ctx->device);
     if (ctx->aux) cudaStreamDestroy(ctx->aux);
     if (ctx->copy_in) cudaStreamDestroy(ctx->copy_in);
+    if (ctx->hstage) cudaFreeHost(ctx->hstage);
     if (ctx->copy_out) cudaStreamDestroy(ctx->copy_out);
     for (cudaEvent_t ev : ctx->pipe_ev) cudaEventDestroy(ev);
     for (cudaStream_t s : ctx->pipe_st) cudaStreamDestroy(s);
@@ -1383,12 +1392,31 @@ static gf_status fill_host_in_place(gf_ctx *ctx, int n, const int32_t *H, const 
                                     const std::vector<size_t> &o_sh, const std::vector<size_t> &o_off,
                                     const std::vector<size_t> &o_pts, const std::vector<size_t> &o_th, size_t o_st,
                                     const std::vector<char> &from_splines, const std::vector<float4 *> &dev_host_rgba,
-                                    const std::vector<const float2 *> &dev_host_guide)
+                                    const std::vector<const float2 *> &dev_host_guide, size_t o_spl, size_t spl_bytes)
 {
     std::vector<gf_frame> fr(n);
     std::vector<gf_spline_frame> sf;
     std::vector<int32_t *> dev_host_shell(n, nullptr);
     std::vector<const uint8_t *> dev_host_labels(n, nullptr);
+    // the splines of every frame: packed into the context's pinned staging buffer
+    // (the previous call synchronised its stream before returning) and sent with
+    // one copy, instead of two copies from pageable memory per frame
+    if (spl_bytes > 0) {
+        if (ctx->hstage_bytes < spl_bytes) {
+            if (ctx->hstage) cudaFreeHost(ctx->hstage);
+            ctx->hstage = nullptr;
+            ctx->hstage_bytes = 0;
+            CK(cudaHostAlloc(&ctx->hstage, spl_bytes, cudaHostAllocDefault));
+            ctx->hstage_bytes = spl_bytes;
+        }
+        char *hs = (char *)ctx->hstage;
+        for (int i = 0; i < n; i++) {
+            if (!from_splines[i] || n_splines[i] <= 0) continue;
+            memcpy(hs + (o_off[i] - o_spl), host_offsets[i], 4 * (size_t)(n_splines[i] + 1));
+            memcpy(hs + (o_pts[i] - o_spl), host_pts[i], 8 * (size_t)n_points[i]);
+        }
+        CK(cudaMemcpyAsync(A + o_spl, hs, spl_bytes, cudaMemcpyHostToDevice, st));
+    }
     for (int i = 0; i < n; i++) {
         const size_t np = (size_t)H[i] * W[i];
         cudaPointerAttributes pa;
@@ -1398,11 +1426,6 @@ static gf_status fill_host_in_place(gf_ctx *ctx, int n, const int32_t *H, const 
         else {
             cudaGetLastError();
             CK(cudaMemcpyAsync(A + o_lab[i], host_labels[i], np, cudaMemcpyHostToDevice, st));
-        }
-        if (from_splines[i] && n_splines[i] > 0) {
-            CK(cudaMemcpyAsync(A + o_off[i], host_offsets[i], 4 * (size_t)(n_splines[i] + 1), cudaMemcpyHostToDevice,
-                               st));
-            CK(cudaMemcpyAsync(A + o_pts[i], host_pts[i], 8 * (size_t)n_points[i], cudaMemcpyHostToDevice, st));
         }
         gf_frame &f = fr[i];
         f.H = H[i];
@@ -1470,7 +1493,7 @@ static gf_status fill_host_in_place(gf_ctx *ctx, int n, const int32_t *H, const 
     // the hole tiles (and the labels, where the device reads them from the host)
     CK(hostio(0, st));
     gf_stats *dst = (gf_stats *)(A + o_st);
-    while ((int)ctx->pipe_ev.size() < 2) {
+    while ((int)ctx->pipe_ev.size() < 3) {
         cudaEvent_t ev;
         CK(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
         ctx->pipe_ev.push_back(ev);
@@ -1480,16 +1503,23 @@ static gf_status fill_host_in_place(gf_ctx *ctx, int n, const int32_t *H, const 
     cudaEvent_t ev_init = all_shell ? ctx->pipe_ev[0] : nullptr;
     gf_status s = GF_OK;
     if (!(params->flags & GF_FLAG_DATA)) {
-        // the guide fields and the colours near the holes on the context's second
-        // stream, beside the fill's preparation (descriptors, init pass, frame order)
+        // beside the fill's preparation (descriptors, init pass, frame order): the
+        // guide fields on the context's second stream and the colours near the holes
+        // on its copy-in stream (the gather is bound by the host link, the guide
+        // kernel by the SMs); the second stream then waits for the gather, so that
+        // guide_ev covers both
         CK(cudaEventRecord(ctx->fork_ev, st));
         CK(cudaStreamWaitEvent(ctx->aux, ctx->fork_ev, 0));
-        if (!sf.empty()) s = guidance_impl(ctx, ctx->garena, (int)sf.size(), sf.data(), eta, ctx->aux);
-        cudaError_t eg = s == GF_OK ? hostio(1, ctx->aux) : cudaSuccess;
+        CK(cudaStreamWaitEvent(ctx->copy_in, ctx->fork_ev, 0));
+        cudaError_t eg = hostio(1, ctx->copy_in);
+        if (eg == cudaSuccess) eg = cudaEventRecord(ctx->pipe_ev[2], ctx->copy_in);
+        if (eg == cudaSuccess && !sf.empty()) s = guidance_impl(ctx, ctx->garena, (int)sf.size(), sf.data(), eta, ctx->aux);
         if (s != GF_OK || eg != cudaSuccess) {
+            cudaStreamSynchronize(ctx->copy_in);
             cudaStreamSynchronize(ctx->aux);
             return s != GF_OK ? s : cuda_fail(ctx, eg);
         }
+        CK(cudaStreamWaitEvent(ctx->aux, ctx->pipe_ev[2], 0));
         CK(cudaEventRecord(ctx->guide_ev, ctx->aux));
         s = enqueue_fill(ctx, n, fr.data(), params, dst, st, ev_init, nullptr, true, nullptr, ctx->guide_ev);
         if (s != GF_OK) {
@@ -1568,10 +1598,17 @@ gf_status gf_fill_batched_host(gf_ctx *ctx, int n, const int32_t *H, const int32
         o_lab[i] = pos; pos = align_up(pos + np, 256);
         o_g[i] = pos; pos = align_up(pos + 8 * np, 256);
         o_sh[i] = pos; pos = align_up(pos + 4 * np, 256);
-        o_off[i] = pos; pos = align_up(pos + (from_splines[i] ? 4 * (size_t)(n_splines[i] + 1) : 0), 256);
-        o_pts[i] = pos; pos = align_up(pos + (from_splines[i] ? 8 * (size_t)n_points[i] : 0), 256);
         o_th[i] = pos; pos = align_up(pos + (size_t)((W[i] + 7) / 8) * ((H[i] + 7) / 8), 256);
     }
+    // every frame's spline offsets and points in one block (one copy from a pinned
+    // staging buffer on the in-place path)
+    const size_t o_spl = pos;
+    for (int i = 0; i < n; i++) {
+        o_off[i] = pos; pos = align_up(pos + (from_splines[i] ? 4 * (size_t)(n_splines[i] + 1) : 0), 16);
+        o_pts[i] = pos; pos = align_up(pos + (from_splines[i] ? 8 * (size_t)n_points[i] : 0), 16);
+    }
+    const size_t spl_bytes = pos - o_spl;
+    pos = align_up(pos, 256);
     for (int i = 0; i < n && sparse; i++) {
         if (host_out_rgba[i] != host_rgba[i]) {
             sparse = false;
@@ -1604,7 +1641,8 @@ gf_status gf_fill_batched_host(gf_ctx *ctx, int n, const int32_t *H, const int32
     cudaStream_t st = (cudaStream_t)stream;
     if (sparse) return fill_host_in_place(ctx, n, H, W, host_labels, host_offsets, host_pts, n_splines, n_points,
                                           eta, host_out_shell, params, host_stats, st, A, o_rgba, o_lab, o_g, o_sh,
-                                          o_off, o_pts, o_th, o_st, from_splines, dev_host_rgba, dev_host_guide);
+                                          o_off, o_pts, o_th, o_st, from_splines, dev_host_rgba, dev_host_guide,
+                                          o_spl, spl_bytes);
     // Chunk pipeline: the frames' inputs are copied in on one stream; each chunk's
     // guide field, fill and output copies run on a stream of their own (with
     // scratch of their own) as soon as its inputs have landed, so chunks whose
