@@ -5,7 +5,8 @@
 // buffer (the fill kernel gathers the colours it needs, near the holes, and
 // writes the hole pixels' colours and the shell map back).
 //
-// Kernels (one frame per blockIdx.y, up to HOSTIO_MAX frames per launch):
+// Kernels (up to HOSTIO_MAX frames per launch; one frame per blockIdx.y, except the
+// gather, a small persistent grid over the launch's frames):
 //   hostio_holes_kernel    per 8x8 tile: does it hold a hole pixel (labels, read
 //                          from the caller's buffer where host_labels is set)
 //   hostio_gather_kernel   host -> device colours of the tiles next to a hole tile
@@ -87,12 +88,11 @@ __global__ void __launch_bounds__(256) hostio_holes_kernel(const __grid_constant
     F.tile_hole[ty * F.TW + tx] = any ? 1 : 0;
 }
 
-__global__ void __launch_bounds__(256) hostio_gather_kernel(const __grid_constant__ HostIOArgs a)
+// A small persistent grid (a third of the SMs; the host link needs only a few
+// hundred KB in flight) that leaves the other SMs to the guide-field kernel running beside
+// it: every warp walks the launch's frames in order and takes every nw-th strip.
+__device__ __forceinline__ void hostio_gather_strip(const HostIOFrame &F, int ty, int s)
 {
-    if ((int)blockIdx.y >= a.n) return;
-    const HostIOFrame &F = a.f[blockIdx.y];
-    int ty, s;
-    if (!hostio_strip(F, ty, s)) return;  // warp-uniform
     const int lane = threadIdx.x & 31;
     const int tx = s * 32 + lane;
     // lane l: is tile 32 s + l next to (or holding) a hole pixel; does it hold one
@@ -130,6 +130,17 @@ __global__ void __launch_bounds__(256) hostio_gather_kernel(const __grid_constan
             if (F.host_rgba && in && ((relm >> (p >> 3)) & 1u)) F.dev_rgba[o] = c[k];
             if (F.host_guide && in && ((ownm >> (p >> 3)) & 1u)) F.dev_guide[o] = g[k];
         }
+    }
+}
+
+__global__ void __launch_bounds__(256) hostio_gather_kernel(const __grid_constant__ HostIOArgs a)
+{
+    const int gw = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const int nw = gridDim.x * (blockDim.x >> 5);
+    for (int fi = 0; fi < a.n; fi++) {
+        const HostIOFrame &F = a.f[fi];
+        const int strips = (F.TW + 31) >> 5;
+        for (int u = gw; u < F.TH * strips; u += nw) hostio_gather_strip(F, u / strips, u - (u / strips) * strips);
     }
 }
 
