@@ -20,7 +20,7 @@ import torch
 from . import _lib
 from ._lib import STATS_BYTES, STATS_DTYPE, GuidefillError, check, lib, make_params
 
-__all__ = ["Context", "context", "fill", "fill_batched", "guidance", "detect_splines", "guidance_auto",
+__all__ = ["Context", "HostBatch", "context", "fill", "fill_batched", "guidance", "detect_splines", "guidance_auto",
            "FillResult", "DetectResult", "GuidefillError", "to_rgba", "STATS_DTYPE"]
 
 
@@ -348,27 +348,47 @@ class Context:
         return outs, det
 
     # ---------------------------------------------------- host-buffer path
-    def fill_batched_host(self, rgba: Sequence[np.ndarray], labels: Sequence[np.ndarray],
-                          guide: Optional[Sequence[Optional[np.ndarray]]], out_rgba: Sequence[np.ndarray],
-                          out_shell: Sequence[np.ndarray], splines=None, eta=3.0, eps=3.0, mu=50.0, c=0.05,
-                          ghost=True, smart=True, rescan=False, snap_tau=1e-5, max_shells=0,
-                          stream=None, data_term=False) -> np.ndarray:
+    def fill_batched_host(self, rgba, labels=None, guide=None, out_rgba=None, out_shell=None, splines=None,
+                          eta=3.0, eps=3.0, mu=50.0, c=0.05, ghost=True, smart=True, rescan=False, snap_tau=1e-5,
+                          max_shells=0, stream=None, data_term=False) -> np.ndarray:
         """Fills frames held in HOST memory (numpy; rgba [H,W,4] float32, labels [H,W] uint8,
         guide [H,W,2] float32 or None with ``splines[i] = (offsets, pts)``); the library
-        copies them to the device, fills, and copies out_rgba / out_shell back.
+        copies them to the device, fills, and copies out_rgba / out_shell back.  ``rgba``
+        may instead be a ``HostBatch`` (the frames' pointer tables built once).
         Returns the stats records."""
+        b = rgba if isinstance(rgba, HostBatch) else HostBatch(rgba, labels, guide, out_rgba, out_shell, splines)
+        st = np.zeros(b.n, dtype=STATS_DTYPE)
+        prm = make_params(eps, mu, c, ghost, smart, rescan, snap_tau, max_shells, data_term)
+        with torch.cuda.device(self.device):
+            check(lib().gf_fill_batched_host(self._h, b.n, b.Hs, b.Ws, b.p_rgba, b.p_labels, b.p_guide, b.ns,
+                                             b.p_offs, b.npts, b.p_pts, C.c_float(eta), b.p_out_rgba,
+                                             b.p_out_shell, C.byref(prm), st.ctypes.data, _stream(stream)),
+                  "gf_fill_batched_host", self._h)
+        return st
+
+
+class HostBatch:
+    """The pointer tables of a batch of host frames for ``Context.fill_batched_host``,
+    built once for frames that are filled repeatedly (a serving loop): the arrays
+    (same arguments as ``fill_batched_host``) are referenced, must stay alive, and
+    must not be resized while the batch is in use.  Every call still reads the
+    inputs from and writes the outputs to these host buffers."""
+
+    def __init__(self, rgba: Sequence[np.ndarray], labels: Sequence[np.ndarray],
+                 guide: Optional[Sequence[Optional[np.ndarray]]], out_rgba: Sequence[np.ndarray],
+                 out_shell: Sequence[np.ndarray], splines=None):
         n = len(rgba)
-        Hs = (C.c_int32 * n)(*[a.shape[0] for a in rgba])
-        Ws = (C.c_int32 * n)(*[a.shape[1] for a in rgba])
+        self.n = n
+        self.Hs = (C.c_int32 * n)(*[a.shape[0] for a in rgba])
+        self.Ws = (C.c_int32 * n)(*[a.shape[1] for a in rgba])
 
         def arr(xs):
             return (C.c_void_p * n)(*[(x.ctypes.data if x is not None else None) for x in xs])
 
-        keep = []
         if guide is None:
             guide = [None] * n
-        ns = (C.c_int32 * n)()
-        npts = (C.c_int32 * n)()
+        self.ns = (C.c_int32 * n)()
+        self.npts = (C.c_int32 * n)()
         offs = [None] * n
         pts = [None] * n
         if splines is not None:
@@ -377,18 +397,13 @@ class Context:
                     continue
                 o = np.ascontiguousarray(sp[0], np.int32)
                 p = np.ascontiguousarray(sp[1], np.float32)
-                keep += [o, p]
                 offs[i], pts[i] = o, p
-                ns[i] = len(o) - 1
-                npts[i] = p.shape[0]
-        st = np.zeros(n, dtype=STATS_DTYPE)
-        prm = make_params(eps, mu, c, ghost, smart, rescan, snap_tau, max_shells, data_term)
-        with torch.cuda.device(self.device):
-            check(lib().gf_fill_batched_host(self._h, n, Hs, Ws, arr(rgba), arr(labels), arr(guide), ns, arr(offs),
-                                             npts, arr(pts), C.c_float(eta), arr(out_rgba), arr(out_shell),
-                                             C.byref(prm), st.ctypes.data, _stream(stream)),
-                  "gf_fill_batched_host", self._h)
-        return st
+                self.ns[i] = len(o) - 1
+                self.npts[i] = p.shape[0]
+        self.p_rgba, self.p_labels, self.p_guide = arr(rgba), arr(labels), arr(guide)
+        self.p_offs, self.p_pts = arr(offs), arr(pts)
+        self.p_out_rgba, self.p_out_shell = arr(out_rgba), arr(out_shell)
+        self._keep = (list(rgba), list(labels), list(guide), offs, pts, list(out_rgba), list(out_shell))
 
 
 _contexts = {}

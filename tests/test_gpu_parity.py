@@ -264,9 +264,14 @@ def test_host_buffer_in_place_moves_only_what_the_fill_touches(pinned):
     labs = [host(lb) for _, lb, _ in cases]
     gds = [None if i in spl else host(np.ascontiguousarray(g, np.float32)) for i, (_, _, g) in enumerate(cases)]
     shells = [np.full(lb.shape, 9, np.int32) for _, lb, _ in cases]
-    for rep in range(2):  # a second call on the filled buffers gives the same result
-        st = ctx.fill_batched_host(bufs, labs, gds, bufs, shells, splines=[spl.get(i) for i in range(5)], eta=3.0,
-                                   mu=10.0)
+    # later calls on the filled buffers give the same result, also through a HostBatch
+    batch = gf.HostBatch(bufs, labs, gds, bufs, shells, splines=[spl.get(i) for i in range(5)])
+    for rep in range(3):
+        if rep == 0:
+            st = ctx.fill_batched_host(bufs, labs, gds, bufs, shells, splines=[spl.get(i) for i in range(5)], eta=3.0,
+                                       mu=10.0)
+        else:
+            st = ctx.fill_batched_host(batch, eta=3.0, mu=10.0)
         for i, r in enumerate(ref):
             sh = r.shell.cpu().numpy()
             assert np.array_equal(shells[i], sh), i
