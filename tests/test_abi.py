@@ -76,3 +76,29 @@ def test_struct_layouts_match_header(tmp_path):
     from paper_1611_05319_gb300 import _lib
     assert sizes == [C.sizeof(_lib.Frame), C.sizeof(_lib.Params), C.sizeof(_lib.SplineFrame), _lib.STATS_BYTES,
                      C.sizeof(_lib.DetectParams), C.sizeof(_lib.DetectFrame), _lib.DetectFrame.result.offset]
+
+
+def test_host_batch_pointer_tables():
+    """HostBatch holds the frames' sizes, data pointers and spline counts that
+    fill_batched_host passes to gf_fill_batched_host, and keeps the arrays alive."""
+    import numpy as np
+    import paper_1611_05319_gb300 as gf
+    rgba = [np.zeros((8 + i, 16, 4), np.float32) for i in range(3)]
+    labels = [np.zeros(a.shape[:2], np.uint8) for a in rgba]
+    shells = [np.zeros(a.shape[:2], np.int32) for a in rgba]
+    guide = [None, np.zeros((9, 16, 2), np.float32), None]
+    splines = [(np.array([0, 3, 5]), np.zeros((5, 2), np.float64)), None, (np.array([0, 2]), np.ones((2, 2)))]
+    b = gf.HostBatch(rgba, labels, guide, rgba, shells, splines=splines)
+    assert b.n == 3
+    assert list(b.Hs) == [8, 9, 10] and list(b.Ws) == [16, 16, 16]
+    assert [b.p_rgba[i] for i in range(3)] == [a.ctypes.data for a in rgba]
+    assert [b.p_out_rgba[i] for i in range(3)] == [a.ctypes.data for a in rgba]
+    assert [b.p_labels[i] for i in range(3)] == [a.ctypes.data for a in labels]
+    assert [b.p_out_shell[i] for i in range(3)] == [a.ctypes.data for a in shells]
+    assert b.p_guide[0] is None and b.p_guide[1] == guide[1].ctypes.data and b.p_guide[2] is None
+    assert list(b.ns) == [2, 0, 1] and list(b.npts) == [5, 0, 2]
+    assert b.p_offs[1] is None and b.p_pts[1] is None
+    # the converted spline arrays (int32 offsets, float32 points) are the ones pointed at
+    offs, pts = b._keep[3], b._keep[4]
+    assert offs[0].dtype == np.int32 and pts[2].dtype == np.float32
+    assert b.p_offs[0] == offs[0].ctypes.data and b.p_pts[2] == pts[2].ctypes.data
